@@ -1,0 +1,270 @@
+"""Throughput of the Hermite half step (DOF-updates/s) on GB300.
+
+Workload: m = 3, periodic 256^3 cube, c = 1, dt = 0.4 h, a seeded random
+state (inputs of 8.6 GB / 17.2 GB per state, far larger than the 129 MB L2, so
+no L2 flush is needed between steps).  A step is one half step of the whole
+grid.  `value` is the mixed-precision path (FP32 arithmetic, FP32 state);
+the plain FP64 path is reported beside it under "fp64".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs independent replicas, one per GPU, no collectives on the
+data path (the method needs none for independent simulations): "scaling":
+"weak", value = all ranks' DOF-updates / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M_ORDER = 3
+N_SIDE = 256
+METRIC = "Hermite DOF-updates/s per half step (m=3, 256^3), FP64 vs mixed at stated error"
+
+
+def dof_per_step(m=M_ORDER, n=N_SIDE):
+    return 2 * (m + 1) ** 3 * n ** 3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def cpu_baseline(max_seconds=30.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: one
+    z-layer of output cells (256 x 256 cells, m = 3) of a seeded state."""
+    from oracle import hermite as oracle
+    import hermite_inputs as HI
+    n = (N_SIDE, N_SIDE, 2)
+    h = (1.0 / N_SIDE,) * 3
+    x = HI.random_state(M_ORDER, n, seed=1)
+    cells, t = 0, 0.0
+    while t < max_seconds / 3 or cells == 0:
+        t0 = time.perf_counter()
+        oracle.half_step(x, M_ORDER, h, 1.0, 0.4 * h[0], 0, z_cells=[0])
+        t += time.perf_counter() - t0
+        cells += N_SIDE * N_SIDE
+        if t > max_seconds:
+            break
+    cores = len(os.sched_getaffinity(0))
+    return {"value": cells * 2 * (M_ORDER + 1) ** 3 / t, "unit": "DOF-updates/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cells // (N_SIDE * N_SIDE)} x one 256x256 z-layer of output cells, m=3, FP64 NumPy",
+            "seconds": t}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self):
+        self.proc, self.path = None, None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", 0)))],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def timed_steps(torch, plan, x, y, steps, warmup):
+    """W untimed then K timed half steps (alternating parity), CUDA events on
+    the launching stream; returns ms per step."""
+    for k in range(warmup):
+        plan.step(x, y, k % 2)
+        x, y = y, x
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(steps):
+        plan.step(x, y, k % 2)
+        x, y = y, x
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_ours(args, rank, world):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1609_09841_gb300 import Plan
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    m, n = M_ORDER, (N_SIDE,) * 3
+    h = (1.0 / N_SIDE,) * 3
+    dt = 0.4 * h[0]
+    dof = dof_per_step()
+    gen = torch.Generator(device="cuda").manual_seed(1609 + rank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # mixed precision: FP32 arithmetic, FP32 state
+    plan = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp32")
+    x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    for k in range(args.warmup):
+        plan.step(x, y, k % 2)
+        x, y = y, x
+    clocks = ClockSampler()
+    barrier()
+    clocks.start()
+    ms = timed_steps(torch, plan, x, y, args.steps, 0)
+    clk = clocks.stop()
+    barrier()
+    ms_max = max_over_ranks(ms)
+    value = world * dof / (ms_max * 1e-3)
+    traffic_alg = plan.elems * 4 * 2          # read + write of the FP32 state
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = traffic_alg / (ms * 1e-3) / 1e9
+    # same arithmetic, FP64 state (loaded, computed in FP32, stored)
+    plan64s = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp64")
+    xd = x.double()
+    yd = torch.empty_like(xd)
+    ms_mixed64 = timed_steps(torch, plan64s, xd, yd, args.steps, args.warmup)
+    # plain FP64
+    plan64 = Plan(m, n, h, 1.0, dt, prec="fp64", state="fp64")
+    ms64 = timed_steps(torch, plan64, xd, yd, args.fp64_steps, min(args.warmup, 3))
+    del xd, yd
+    # end to end through the C ABI with pinned host buffers (FP32 state)
+    hx = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
+    hy = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
+    hx.copy_(x)
+    plan.step(hx.numpy(), hy.numpy(), 0)
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        plan.step(hx.numpy(), hy.numpy(), k % 2)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(e2e_s)
+    bytes_state = plan.elems * 4
+    out = {
+        "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "m=3 periodic 256^3 cube, c=1, dt=0.4h, seeded N(0,1) state, one half step per "
+                               "step, FP32 arithmetic and FP32 state; inputs 8.6 GB > L2 (no flush)",
+                   "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
+                   "variant": "fused", "dof_per_step": dof},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json)",
+                     "kernel": "fused_step_kernel<float,float,4,...>"},
+        "fp64": {"value": world * dof / (max_over_ranks(ms64) * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps,
+                 "dtype": "f64", "state": "fp64"},
+        "mixed_fp64_state": {"value": world * dof / (max_over_ranks(ms_mixed64) * 1e-3), "ms_per_step": ms_mixed64,
+                             "hbm_frac": plan.elems * 8 * 2 / (ms_mixed64 * 1e-3) / 1e9 / hbm_peak},
+        "speedup_mixed_vs_fp64": ms64 / ms,
+        "e2e": {"value": world * dof / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": bytes_state,
+                "d2h_bytes_per_step": bytes_state, "seconds_per_step": e2e_s},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands on the host cores, each step a bounded
+    sample (one 256x256 z-layer of output cells) of the same workload."""
+    from oracle import hermite as oracle
+    import hermite_inputs as HI
+    n = (N_SIDE, N_SIDE, 2)
+    h = (1.0 / N_SIDE,) * 3
+    x = HI.random_state(M_ORDER, n, seed=1)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated to bound the run
+    steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.half_step(x, M_ORDER, h, 1.0, 0.4 * h[0], 0, z_cells=[0])
+    t = (time.perf_counter() - t0) / steps
+    dofs = N_SIDE * N_SIDE * 2 * (M_ORDER + 1) ** 3
+    v = dofs / t
+    cores = len(os.sched_getaffinity(0))
+    sample = "one 256x256 z-layer of output cells per step (m=3, FP64 NumPy oracle)"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF-updates/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "m=3 periodic 256^3 cube, c=1, dt=0.4h, seeded N(0,1) state (bounded sample)"},
+            "cpu_baseline": {"value": v, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+/*
+ * hermite.h -- C ABI of libhermite: the Hermite half step of the 3-D scalar
+ * linear wave equation u_t = v, v_t = c^2 (u_xx + u_yy + u_zz) on a staggered
+ * primal/dual periodic tensor grid, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method is that of Vargas, Chan, Hagstrom and Warburton, "GPU
+ * Acceleration of Hermite Methods for the Simulation of Wave Propagation"
+ * (arXiv:1609.09841):
+ *   - Eq. 2: each node stores the scaled derivatives
+ *       h1^i1 h2^i2 h3^i3 / (i1! i2! i3!) d^i f,  0 <= i1, i2, i3 <= m,
+ *     of each field f in {u, v};
+ *   - Eq. 3, Sec. 3.1, Alg. 1/2: on every cell the 8 corner nodes' data are
+ *     interpolated, dimension by dimension, into a polynomial of degree 2m+1
+ *     per variable whose coefficients are the scaled derivatives at the cell
+ *     centre;
+ *   - Eq. 4, Alg. 3/4: that polynomial is evolved locally over half a time
+ *     step (here classical RK4, equal to a 4-term Taylor series for this
+ *     linear operator);
+ *   - Sec. 2: its coefficients of order <= m become the data of the dual
+ *     node at the cell centre; the next half step maps dual -> primal.
+ *
+ * Conventions (all entry points)
+ *   m           order: 1, 2 or 3 (the paper's N).  M = m+1 derivative orders
+ *               per dimension, P = 2m+2 coefficients per dimension.
+ *   grid[3]     (n1, n2, n3) = nodes along (x1, x2, x3); the grid is periodic.
+ *   h[3]        (h1, h2, h3) node spacings (> 0).
+ *   dt          the FULL time step of Eq. 4; every hermite_step advances the
+ *               state by dt/2.
+ *   state       2 * M^3 * n1*n2*n3 values, layout [f][i3][i2][i1][z][y][x]
+ *               (field, derivative order along x3, x2, x1, then node with x1
+ *               fastest: the tensor u[m3][m2][m1][n3][n2][n1] of Sec. 3.1 for
+ *               each field).  Element type: double for HERMITE_STATE_FP64,
+ *               float for HERMITE_STATE_FP32.  Buffers are contiguous and owned
+ *               by the caller; device buffers must be 16-byte aligned.
+ *   parity      0: the input lives on the primal grid (node i at i*h) and the
+ *               output on the dual grid (node i at (i+1/2)*h, the centre of the
+ *               cell with primal corners i, i+1); 1: dual -> primal (primal node
+ *               i is the centre of the cell with dual corners i-1, i).
+ *   stream      a cudaStream_t cast to void* (NULL = the legacy default stream).
+ *               All work is enqueued on it and the calls return without waiting,
+ *               except hermite_error, hermite_last_status and host-buffer steps.
+ *
+ * Errors: every int-returning call returns HERMITE_OK (0) or a negative
+ * hermite_status; hermite_last_error() then describes the failure (a
+ * thread-local string owned by the library).  Invalid arguments never reach
+ * the GPU.
+ */
+#ifndef HERMITE_H
+#define HERMITE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hermite_plan_s *hermite_plan_t; /* opaque; owned by the library */
+
+enum hermite_status {
+  HERMITE_OK = 0,
+  HERMITE_EINVAL = -1,       /* bad argument: order, sizes, pointers, parity, in == out */
+  HERMITE_ENOMEM = -2,       /* a device or host allocation failed */
+  HERMITE_ECUDA = -3,        /* a CUDA runtime call or kernel launch failed */
+  HERMITE_EUNSUPPORTED = -4, /* combination of precision / state type / variant not provided */
+  HERMITE_EUNSTABLE = -5,    /* c*(dt/2)/h_k above the stability limit of order m */
+  HERMITE_ETIMEOUT = -6,     /* a bounded device-side wait gave up (batched scheduler) */
+  HERMITE_ENONFINITE = -7    /* hermite_error saw a NaN or Inf */
+};
+
+/* Arithmetic of the contractions (interpolation and evolution). */
+enum hermite_prec {
+  HERMITE_FP64 = 0, /* FP64 throughout (state must be FP64) */
+  HERMITE_FP32 = 1  /* FP32 contractions, state FP32 or FP64 (loaded, computed in FP32, stored) */
+};
+
+enum hermite_state_type { HERMITE_STATE_FP64 = 0, HERMITE_STATE_FP32 = 1 };
+
+/* Kernel design.  FUSED: one kernel per half step does interpolation,
+ * evolution and truncation per cell (Sec. 3.3's monolithic design, re-done
+ * with a Kronecker-sum factorisation of the whole half step).  SPLIT: an
+ * interpolation kernel writes the cell polynomials to a workspace and an
+ * evolution kernel runs the Taylor/RK4 loop on them (Sec. 3.1 + Sec. 3.2),
+ * processed in z-slabs to bound the workspace.  AUTO = FUSED. */
+enum hermite_variant { HERMITE_AUTO = 0, HERMITE_FUSED = 1, HERMITE_SPLIT = 2 };
+
+/* Create a plan.  Checks every argument, the stability limit
+ * (max_k c*(dt/2)/h_k <= hermite_stability_limit(m)) and builds the 1-D
+ * operator tables in exact rational arithmetic on the host.  No GPU work and
+ * no device allocation happen here, so a plan can be made without a GPU.
+ * Returns EINVAL, EUNSTABLE, EUNSUPPORTED or ENOMEM; *out is NULL on failure. */
+int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c,
+                 double dt, int prec, int state_dtype, int variant);
+
+/* One half step (Sec. 2): out = S_parity(in).  in and out are either both
+ * device pointers (the step is only enqueued on `stream`) or both host
+ * pointers (the library copies in -> device, steps and copies back through
+ * plan-owned staging buffers, synchronising `stream` before it returns).
+ * in == out (or overlapping buffers) is EINVAL: a half step is not in place. */
+int hermite_step(hermite_plan_t plan, const void *in_state, void *out_state, int parity,
+                 void *stream);
+
+/* Discrete adjoint of hermite_step: in_adj = S_parity^T out_adj, where
+ * out_adj lives on the output grid of the forward step with that parity and
+ * in_adj on its input grid.  Same buffer rules as hermite_step (device
+ * pointers only). */
+int hermite_adjoint_step(hermite_plan_t plan, const void *out_adj, void *in_adj, int parity,
+                         void *stream);
+
+/* Error norms of `state` (the plan's state type) against `ref` (always FP64,
+ * same layout), both device pointers, over the components selected by
+ * component_mask: bit0 field u, bit1 field v, bit2 all derivative orders
+ * (else the values i = (0,0,0) only).  out[0] = max|a-b|, out[1] =
+ * max|a-b| / max|b|, out[2] = sqrt(mean (a-b)^2), out[3] = ||a-b||_2/||b||_2.
+ * FP64 reduction on the device; synchronises `stream`.  Returns ENONFINITE
+ * (with out filled) if any selected entry of either array is NaN or Inf. */
+int hermite_error(hermite_plan_t plan, const void *state, const void *ref, unsigned component_mask,
+                  double out[4], void *stream);
+
+/* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
+size_t hermite_state_elems(hermite_plan_t plan);
+
+/* Largest c*(dt/2)/h for which the half step of order m (1..3) is stable,
+ * from the Fourier symbol of the isotropic half step; 0 for other m. */
+double hermite_stability_limit(int m);
+
+/* Copy the plan's 1-D interpolation operator H (P x P, row-major, H[j][(side,i)]:
+ * monomial coefficient j from [left i = 0..m, right i = 0..m], Sec. 3.1) to
+ * out[0 .. P*P-1].  Host only; for inspection and tests. */
+int hermite_plan_operator(hermite_plan_t plan, double *out);
+
+/* Release the plan and every device buffer it owns (workspace, staging,
+ * reduction scratch).  NULL is ignored. */
+void hermite_destroy(hermite_plan_t plan);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *hermite_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HERMITE_H */

@@ -1,0 +1,5 @@
+"""Hermite half step of the 3-D scalar wave equation on one GB300 (sm_103a).
+
+``Plan`` wraps the C ABI of libhermite (include/hermite.h); the arithmetic
+runs only in that CUDA library, which must be built (``build.build()``)."""
+from .hermite import Plan, stability_limit  # noqa: F401

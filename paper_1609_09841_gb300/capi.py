@@ -1,0 +1,73 @@
+"""ctypes declarations of libhermite's C ABI (include/hermite.h).
+
+Argument marshalling only: every step of the half step runs in the CUDA
+library.  Importing this module loads libhermite.so and raises if it is
+missing -- there is no fallback implementation."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhermite.so")
+
+HERMITE_OK = 0
+HERMITE_EINVAL = -1
+HERMITE_ENOMEM = -2
+HERMITE_ECUDA = -3
+HERMITE_EUNSUPPORTED = -4
+HERMITE_EUNSTABLE = -5
+HERMITE_ETIMEOUT = -6
+HERMITE_ENONFINITE = -7
+
+HERMITE_FP64 = 0
+HERMITE_FP32 = 1
+HERMITE_STATE_FP64 = 0
+HERMITE_STATE_FP32 = 1
+HERMITE_AUTO = 0
+HERMITE_FUSED = 1
+HERMITE_SPLIT = 2
+
+STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED",
+                -5: "EUNSTABLE", -6: "ETIMEOUT", -7: "ENONFINITE"}
+
+
+class HermiteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhermite.so not built ({LIB_PATH}); run paper_1609_09841_gb300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, U, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_size_t
+    IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "hermite_plan": (I, [ctypes.POINTER(P), I, IP, DP, D, D, I, I, I]),
+        "hermite_step": (I, [P, P, P, I, P]),
+        "hermite_adjoint_step": (I, [P, P, P, I, P]),
+        "hermite_error": (I, [P, P, P, U, DP, P]),
+        "hermite_state_elems": (S, [P]),
+        "hermite_stability_limit": (D, [I]),
+        "hermite_plan_operator": (I, [P, DP]),
+        "hermite_destroy": (None, [P]),
+        "hermite_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def last_error():
+    return lib.hermite_last_error().decode()
+
+
+def check(code):
+    if code != HERMITE_OK:
+        raise HermiteError(code, last_error())
+    return code

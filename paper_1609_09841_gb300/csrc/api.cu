@@ -1,0 +1,323 @@
+// C ABI of libhermite (include/hermite.h): plans, argument checks, dispatch to
+// the fused or split kernels, host-buffer staging and the error norms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/hermite.h"
+#include "hermite_impl.h"
+
+using namespace hermite;
+
+struct hermite_plan_s {
+  int m;
+  int n[3];
+  double h[3];
+  double c, dt, tau;
+  int prec, state, variant;
+  size_t elems;
+  double H[64];
+  StepCoeffs<double> fwd, adj;
+  StepCoeffs<float> fwd32, adj32;
+  InterpCoeffs<double> interp;
+  EvolveParams evolve;
+  int zchunk;               // fused kernel: cells per CTA along x3
+  size_t ws_limit;          // split variant: workspace budget in bytes
+  void *ws = nullptr;       // split workspace (device), grown on demand
+  size_t ws_bytes = 0;
+  void *stage[2] = {nullptr, nullptr};  // host-buffer steps: device copies of in / out
+  double *red = nullptr;    // error reduction scratch (device)
+  double *red_host = nullptr;  // pinned result
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  return fail(HERMITE_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Stability limit of c*tau/h per order, from the largest spectral radius of
+// the Fourier symbol of the isotropic half step over theta in [0, pi]^3
+// (bisection to 1e-3, rounded down).
+const double kStabilityLimit[4] = {0.0, 0.45, 0.30, 0.26};
+
+size_t state_bytes(const hermite_plan_s *p) {
+  return p->elems * (p->state == HERMITE_STATE_FP64 ? sizeof(double) : sizeof(float));
+}
+
+enum PtrKind { kHostPtr, kDevicePtr, kBadPtr };
+
+PtrKind classify(const void *ptr) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return kBadPtr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevicePtr;
+  return kHostPtr;
+}
+
+bool overlaps(const void *a, const void *b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+int check_device_pair(const hermite_plan_s *p, const void *in, void *out) {
+  if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
+  if (overlaps(in, out, state_bytes(p)))
+    return fail(HERMITE_EINVAL, "input and output states overlap (a half step is not in place)");
+  if (((uintptr_t)in | (uintptr_t)out) & 15u)
+    return fail(HERMITE_EINVAL, "device state pointers must be 16-byte aligned");
+  return HERMITE_OK;
+}
+
+Geom geom_of(const hermite_plan_s *p, int s) {
+  Geom g;
+  g.nx = p->n[0];
+  g.ny = p->n[1];
+  g.nz = p->n[2];
+  g.s = s;
+  return g;
+}
+
+int ensure_ws(hermite_plan_s *p, size_t bytes) {
+  if (p->ws_bytes >= bytes) return HERMITE_OK;
+  if (p->ws) cudaFree(p->ws);
+  p->ws = nullptr;
+  p->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&p->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HERMITE_ENOMEM, "split workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  p->ws_bytes = bytes;
+  return HERMITE_OK;
+}
+
+// Device-pointer half step of either direction (adjoint: transposed tables,
+// mirrored corner offset).
+int run_step(hermite_plan_s *p, const void *in, void *out, int parity, bool adjoint, cudaStream_t st) {
+  const int s_fwd = parity == 0 ? 0 : -1;
+  const int s = adjoint ? -s_fwd - 1 : s_fwd;
+  const Geom g = geom_of(p, s);
+  const bool split = p->variant == HERMITE_SPLIT && !adjoint;
+  cudaError_t e = cudaSuccess;
+  if (!split) {
+    if (p->prec == HERMITE_FP64)
+      e = launch_fused_f64(p->m, (const double *)in, (double *)out, g, adjoint ? p->adj : p->fwd, p->zchunk, st);
+    else
+      e = launch_fused_f32(p->m, p->state == HERMITE_STATE_FP64 ? kF64 : kF32, in, out, g,
+                           adjoint ? p->adj32 : p->fwd32, p->zchunk, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fused half-step launch");
+    return HERMITE_OK;
+  }
+  // Split pair, z-slab by z-slab so that the workspace stays within budget.
+  const int P = 2 * p->m + 2;
+  const size_t elt = p->prec == HERMITE_FP64 ? sizeof(double) : sizeof(float);
+  const size_t per_layer = (size_t)2 * P * P * P * p->n[0] * p->n[1] * elt;
+  int nzl = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->n[2], p->ws_limit / per_layer));
+  int rc = ensure_ws(p, per_layer * nzl);
+  if (rc) return rc;
+  const int compute = p->prec == HERMITE_FP64 ? kF64 : kF32;
+  const int state = p->state == HERMITE_STATE_FP64 ? kF64 : kF32;
+  for (int z0 = 0; z0 < p->n[2]; z0 += nzl) {
+    const int nl = std::min(nzl, p->n[2] - z0);
+    e = launch_interp(p->m, state, compute, in, p->ws, g, z0, nl, p->interp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "interpolation kernel launch");
+    e = launch_evolve(p->m, state, compute, p->ws, out, g, z0, nl, p->evolve, st);
+    if (e != cudaSuccess) return cuda_fail(e, "evolution kernel launch");
+  }
+  return HERMITE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hermite_last_error(void) { return g_last_error.c_str(); }
+
+double hermite_stability_limit(int m) { return (m >= 1 && m <= 3) ? kStabilityLimit[m] : 0.0; }
+
+int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c, double dt,
+                 int prec, int state_dtype, int variant) {
+  g_last_error.clear();
+  if (!out) return fail(HERMITE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || m > 3) return fail(HERMITE_EINVAL, "order m = %d not in 1..3", m);
+  if (!grid || !h) return fail(HERMITE_EINVAL, "grid or h is NULL");
+  for (int k = 0; k < 3; ++k) {
+    if (grid[k] < 1 || grid[k] > (1 << 20)) return fail(HERMITE_EINVAL, "grid[%d] = %d out of range", k, grid[k]);
+    if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(HERMITE_EINVAL, "h[%d] must be positive", k);
+  }
+  if (!(c > 0.0) || !std::isfinite(c)) return fail(HERMITE_EINVAL, "wave speed c must be positive");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
+  if (prec != HERMITE_FP64 && prec != HERMITE_FP32) return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
+  if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
+    return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
+  if (prec == HERMITE_FP64 && state_dtype != HERMITE_STATE_FP64)
+    return fail(HERMITE_EUNSUPPORTED, "FP64 arithmetic needs an FP64 state");
+  if (variant != HERMITE_AUTO && variant != HERMITE_FUSED && variant != HERMITE_SPLIT)
+    return fail(HERMITE_EINVAL, "variant %d unknown", variant);
+  const double tau = 0.5 * dt;
+  for (int k = 0; k < 3; ++k) {
+    const double lam = c * tau / h[k];
+    if (lam > kStabilityLimit[m] * (1.0 + 1e-12))
+      return fail(HERMITE_EUNSTABLE, "c*(dt/2)/h[%d] = %.6g above the stability limit %.3g of order %d", k, lam,
+                  kStabilityLimit[m], m);
+  }
+  const size_t nodes = (size_t)grid[0] * grid[1] * grid[2];
+  hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
+  if (!p) return fail(HERMITE_ENOMEM, "plan allocation");
+  p->m = m;
+  for (int k = 0; k < 3; ++k) {
+    p->n[k] = grid[k];
+    p->h[k] = h[k];
+  }
+  p->c = c;
+  p->dt = dt;
+  p->tau = tau;
+  p->prec = prec;
+  p->state = state_dtype;
+  p->variant = variant == HERMITE_AUTO ? HERMITE_FUSED : variant;
+  p->elems = (size_t)2 * (m + 1) * (m + 1) * (m + 1) * nodes;
+  build_H(m, p->H);
+  build_step_coeffs(m, h, c, tau, false, &p->fwd);
+  build_step_coeffs(m, h, c, tau, true, &p->adj);
+  p->fwd32 = cast_coeffs<float>(p->fwd);
+  p->adj32 = cast_coeffs<float>(p->adj);
+  build_interp_coeffs(m, &p->interp);
+  p->evolve.tau = tau;
+  for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
+  p->zchunk = 16;
+  p->ws_limit = (size_t)1 << 30;
+  *out = p;
+  return HERMITE_OK;
+}
+
+size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
+
+int hermite_plan_operator(hermite_plan_t p, double *out) {
+  if (!p || !out) return fail(HERMITE_EINVAL, "null argument");
+  const int P = 2 * p->m + 2;
+  std::memcpy(out, p->H, sizeof(double) * P * P);
+  return HERMITE_OK;
+}
+
+int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
+  if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
+  if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const PtrKind ki = classify(in), ko = classify(out);
+  if (ki == kBadPtr || ko == kBadPtr) return fail(HERMITE_ECUDA, "cannot query pointer attributes (no CUDA device?)");
+  if (ki != ko) return fail(HERMITE_EINVAL, "in and out must both be device or both be host buffers");
+  if (ki == kDevicePtr) {
+    int rc = check_device_pair(p, in, out);
+    if (rc) return rc;
+    return run_step(p, in, out, parity, false, st);
+  }
+  // Host buffers: copy in, step, copy out through plan-owned device buffers.
+  const size_t bytes = state_bytes(p);
+  if (overlaps(in, out, bytes)) return fail(HERMITE_EINVAL, "input and output states overlap");
+  for (int k = 0; k < 2; ++k)
+    if (!p->stage[k]) {
+      cudaError_t e = cudaMalloc(&p->stage[k], bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->stage[k] = nullptr;
+        return fail(HERMITE_ENOMEM, "staging buffer of %zu bytes", bytes);
+      }
+    }
+  cudaError_t e = cudaMemcpyAsync(p->stage[0], in, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+  int rc = run_step(p, p->stage[0], p->stage[1], parity, false, st);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out, p->stage[1], bytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  return HERMITE_OK;
+}
+
+int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, int parity, void *stream) {
+  if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
+  int rc = check_device_pair(p, out_adj, in_adj);
+  if (rc) return rc;
+  if (classify(out_adj) != kDevicePtr || classify(in_adj) != kDevicePtr)
+    return fail(HERMITE_EINVAL, "adjoint steps take device buffers");
+  return run_step(p, out_adj, in_adj, parity, true, (cudaStream_t)stream);
+}
+
+int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned mask, double out[4],
+                  void *stream) {
+  if (!p || !state || !ref || !out) return fail(HERMITE_EINVAL, "null argument");
+  if ((mask & 3u) == 0) return fail(HERMITE_EINVAL, "component mask selects no field");
+  if (classify(state) != kDevicePtr || classify(ref) != kDevicePtr)
+    return fail(HERMITE_EINVAL, "hermite_error takes device buffers");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = error_blocks();
+  if (!p->red) {
+    cudaError_t e = cudaMalloc(&p->red, sizeof(double) * (size_t)(blocks + 1) * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->red = nullptr;
+      return fail(HERMITE_ENOMEM, "reduction scratch");
+    }
+    e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->red_host = nullptr;
+      return fail(HERMITE_ENOMEM, "pinned result buffer");
+    }
+  }
+  const size_t plane = (size_t)p->n[0] * p->n[1] * p->n[2];
+  cudaError_t e = launch_error(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, state, (const double *)ref, p->m,
+                               plane, mask, p->red + 8, blocks, p->red, st);
+  if (e != cudaSuccess) return cuda_fail(e, "error-norm launch");
+  e = cudaMemcpyAsync(p->red_host, p->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "norm copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  const double *r = p->red_host;
+  const int nc = (p->m + 1) * (p->m + 1) * (p->m + 1);
+  const double count = (double)plane * (((mask & 1u) ? 1 : 0) + ((mask & 2u) ? 1 : 0)) * ((mask & 4u) ? nc : 1);
+  out[0] = r[0];
+  out[1] = r[1] > 0 ? r[0] / r[1] : INFINITY;
+  out[2] = std::sqrt(r[2] / count);
+  out[3] = r[3] > 0 ? std::sqrt(r[2] / r[3]) : INFINITY;
+  if (r[4] > 0) return fail(HERMITE_ENONFINITE, "%.0f non-finite entries", r[4]);
+  return HERMITE_OK;
+}
+
+void hermite_destroy(hermite_plan_t p) {
+  if (!p) return;
+  if (p->ws) cudaFree(p->ws);
+  for (int k = 0; k < 2; ++k)
+    if (p->stage[k]) cudaFree(p->stage[k]);
+  if (p->red) cudaFree(p->red);
+  if (p->red_host) cudaFreeHost(p->red_host);
+  delete p;
+}
+
+}  // extern "C"

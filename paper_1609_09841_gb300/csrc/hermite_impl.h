@@ -1,0 +1,95 @@
+// Internal declarations of libhermite: operator tables and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace hermite {
+
+constexpr int kMaxM = 4;  // largest M = m + 1
+
+// Tables of the fused half step.  For one cell and one input field the half
+// step is the Kronecker sum  sum_s beta_s sum_{a+b+c=s} Gz_c (x) Gy_b (x) Gx_a
+// (a, b, c <= 2), where G_a = T1 (lam^2 d^2/dxi^2)^a / a! H is the 1-D factor
+// "interpolate (Sec. 3.1), differentiate twice a times (Alg. 3), keep orders
+// <= m (Sec. 2)" and beta_s couples the fields through the 4-term Taylor
+// series of RK4 (Alg. 4).  Every G_a satisfies G[r][(left, i)] =
+// (-1)^(r+i) G[r][(right, i)], so only the right block is stored and the
+// kernels apply it to R_i + (-1)^(r+i) L_i (an even/odd butterfly).
+template <typename T>
+struct StepCoeffs {
+  T gx[3][16];        // right block of G_a along x1, [a][r * 4 + i]
+  T gy[3][16];        // same along x2
+  T kz[2][2][3][16];  // [f_out][f_in][grade g][r * 4 + i] = sum_c beta_{g+c} Gz_c (right block)
+};
+
+// Tables of the split pair: the right block of H (interpolation) and the
+// constants of the local evolution.
+template <typename T>
+struct InterpCoeffs {
+  T hr[8][4];  // H[r][M + i], r < P
+};
+struct EvolveParams {
+  double tau;     // half-step duration dt / 2
+  double c2h[3];  // c^2 / h_k^2 along x1, x2, x3
+};
+
+// Host-side construction (exact rational arithmetic, then rounded once).
+void build_H(int m, double *H);  // P x P row-major
+void build_step_coeffs(int m, const double h[3], double c, double tau, bool adjoint,
+                       StepCoeffs<double> *out);
+void build_interp_coeffs(int m, InterpCoeffs<double> *out);
+
+template <typename T>
+StepCoeffs<T> cast_coeffs(const StepCoeffs<double> &in) {
+  StepCoeffs<T> o;
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 16; ++k) {
+      o.gx[a][k] = (T)in.gx[a][k];
+      o.gy[a][k] = (T)in.gy[a][k];
+    }
+  for (int f = 0; f < 2; ++f)
+    for (int g = 0; g < 2; ++g)
+      for (int s = 0; s < 3; ++s)
+        for (int k = 0; k < 16; ++k) o.kz[f][g][s][k] = (T)in.kz[f][g][s][k];
+  return o;
+}
+
+// Grid geometry of one launch.
+struct Geom {
+  int nx, ny, nz;
+  int s;  // corner offset: corners of output node o are o + s + {0, 1} per dimension
+};
+
+// Launch configuration of the fused kernel (chosen per m and precision).
+struct FusedLaunch {
+  int zchunk;  // cells per CTA along x3
+};
+
+enum StateKind { kF64 = 0, kF32 = 1 };
+
+// Fused half step (forward or adjoint: the adjoint is the same kernel with
+// transposed tables and the mirrored offset).
+cudaError_t launch_fused_f64(int m, const double *in, double *out, const Geom &g,
+                             const StepCoeffs<double> &co, int zchunk, cudaStream_t st);
+cudaError_t launch_fused_f32(int m, int state, const void *in, void *out, const Geom &g,
+                             const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+
+// Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
+// output z-layers [z0, z0 + nzl); evolution reads it and writes the new node
+// data of those layers.
+cudaError_t launch_interp(int m, int state, int compute, const void *in, void *ru, const Geom &g,
+                          int z0, int nzl, const InterpCoeffs<double> &co, cudaStream_t st);
+cudaError_t launch_evolve(int m, int state, int compute, const void *ru, void *out, const Geom &g,
+                          int z0, int nzl, const EvolveParams &ep, cudaStream_t st);
+
+// FP64 error reduction.  `partial` holds blocks * 8 doubles of scratch,
+// `result` 8 doubles.
+cudaError_t launch_error(int state, const void *a, const double *b, int m, size_t plane,
+                         unsigned mask, double *partial, int blocks, double *result,
+                         cudaStream_t st);
+int error_blocks();
+
+}  // namespace hermite

@@ -1,0 +1,176 @@
+// Host construction of the 1-D operators in exact rational arithmetic.
+//
+// H (Sec. 3.1) maps the data of a cell edge -- [left node: scaled derivatives
+// i = 0..m, right node: i = 0..m] with the nodes at xi = -1/2 and +1/2 -- to
+// the P = 2m+2 monomial coefficients of the interpolant in xi = (x - x_c)/h
+// (Eq. 3).  The node data of p(xi) = sum c_j xi^j are
+// (1/i!) p^(i)(xi0) = sum_j C(j, i) xi0^(j-i) c_j (Eq. 2 in the scaled
+// variable); H is the inverse of that matrix, computed here by Gauss-Jordan
+// elimination on fractions of 128-bit integers and rounded to double once.
+#include <cstdint>
+#include <cstdlib>
+
+#include "hermite_impl.h"
+
+namespace hermite {
+namespace {
+
+using i128 = __int128;
+
+i128 gcd128(i128 a, i128 b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b != 0) {
+    i128 t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+struct Q {
+  i128 n = 0, d = 1;
+  Q() = default;
+  Q(i128 num, i128 den = 1) : n(num), d(den) { norm(); }
+  void norm() {
+    if (d < 0) {
+      n = -n;
+      d = -d;
+    }
+    i128 g = gcd128(n, d);
+    if (g > 1) {
+      n /= g;
+      d /= g;
+    }
+  }
+  double to_double() const { return (double)((long double)n / (long double)d); }
+};
+Q operator-(const Q &a, const Q &b) { return Q(a.n * b.d - b.n * a.d, a.d * b.d); }
+Q operator*(const Q &a, const Q &b) { return Q(a.n * b.n, a.d * b.d); }
+Q operator/(const Q &a, const Q &b) { return Q(a.n * b.d, a.d * b.n); }
+
+i128 binom(int n, int k) {
+  i128 r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return r;
+}
+
+// Exact H for order m, H[j][col], P x P.
+void exact_H(int m, Q H[8][8]) {
+  const int M = m + 1, P = 2 * m + 2;
+  Q A[8][16];
+  for (int r = 0; r < P; ++r)
+    for (int c = 0; c < 2 * P; ++c) A[r][c] = Q(0);
+  for (int side = 0; side < 2; ++side) {
+    const Q xi0(side == 0 ? -1 : 1, 2);
+    for (int i = 0; i < M; ++i)
+      for (int j = i; j < P; ++j) {
+        Q p(1);
+        for (int e = 0; e < j - i; ++e) p = p * xi0;
+        A[side * M + i][j] = Q(binom(j, i)) * p;
+      }
+  }
+  for (int r = 0; r < P; ++r) A[r][P + r] = Q(1);
+  for (int col = 0; col < P; ++col) {
+    int piv = col;
+    while (A[piv][col].n == 0) ++piv;
+    if (piv != col)
+      for (int c = 0; c < 2 * P; ++c) {
+        Q t = A[col][c];
+        A[col][c] = A[piv][c];
+        A[piv][c] = t;
+      }
+    const Q p = A[col][col];
+    for (int c = 0; c < 2 * P; ++c) A[col][c] = A[col][c] / p;
+    for (int r = 0; r < P; ++r) {
+      if (r == col || A[r][col].n == 0) continue;
+      const Q f = A[r][col];
+      for (int c = 0; c < 2 * P; ++c) A[r][c] = A[r][c] - f * A[col][c];
+    }
+  }
+  for (int r = 0; r < P; ++r)
+    for (int c = 0; c < P; ++c) H[r][c] = A[r][P + c];
+}
+
+}  // namespace
+
+void build_H(int m, double *H) {
+  const int P = 2 * m + 2;
+  Q Hq[8][8];
+  exact_H(m, Hq);
+  for (int r = 0; r < P; ++r)
+    for (int c = 0; c < P; ++c) H[r * P + c] = Hq[r][c].to_double();
+}
+
+void build_interp_coeffs(int m, InterpCoeffs<double> *out) {
+  const int M = m + 1, P = 2 * m + 2;
+  Q Hq[8][8];
+  exact_H(m, Hq);
+  for (int r = 0; r < 8; ++r)
+    for (int i = 0; i < 4; ++i) out->hr[r][i] = (r < P && i < M) ? Hq[r][M + i].to_double() : 0.0;
+}
+
+// G_a[r][col] = (r+2a)!/r! H[r+2a][col] (zero when r + 2a > 2m+1): the
+// coefficients of order r <= m of d^{2a}/dxi^{2a} applied to the interpolant
+// (Alg. 3 twice per power of the Laplacian, then truncation of Sec. 2).
+void build_step_coeffs(int m, const double h[3], double c, double tau, bool adjoint,
+                       StepCoeffs<double> *out) {
+  const int M = m + 1, P = 2 * m + 2;
+  Q Hq[8][8];
+  exact_H(m, Hq);
+  double G[3][3][4][8];  // [dim][a][r][col], scaled by lam_k^(2a) / a!
+  for (int k = 0; k < 3; ++k) {
+    const double lam2 = (c * tau / h[k]) * (c * tau / h[k]);
+    for (int a = 0; a < 3; ++a) {
+      const double scale = (a == 0 ? 1.0 : (a == 1 ? lam2 : 0.5 * lam2 * lam2));
+      for (int r = 0; r < 4; ++r)
+        for (int col = 0; col < 8; ++col) {
+          double v = 0.0;
+          if (r < M && col < P && r + 2 * a < P) {
+            i128 fac = 1;
+            for (int q = r + 1; q <= r + 2 * a; ++q) fac *= q;
+            v = (Q(fac) * Hq[r + 2 * a][col]).to_double() * scale;
+          }
+          G[k][a][r][col] = v;
+        }
+    }
+  }
+  // Right block (forward) or transposed left block (adjoint).
+  double GR[3][3][16];
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a)
+      for (int r = 0; r < 4; ++r)
+        for (int i = 0; i < 4; ++i) {
+          double v = 0.0;
+          if (r < M && i < M) v = adjoint ? G[k][a][i][r] : G[k][a][r][M + i];
+          GR[k][a][r * 4 + i] = v;
+        }
+  // Field coupling of the 4-term Taylor series E = sum_q (tau L)^q / q!,
+  // L = [[0, I], [c^2 Delta, 0]], written per grade s of
+  // Lambda^s = s! sum_{a+b+c=s} prod_k (lam_k^2 d^2/dxi_k^2)^{a_k} / a_k!.
+  double beta[2][2][3];
+  const double uu[3] = {1.0, 0.5, 1.0 / 12.0};
+  const double uv[3] = {tau, tau / 6.0, 0.0};
+  const double vu[3] = {0.0, 1.0 / tau, 1.0 / (3.0 * tau)};
+  for (int s = 0; s < 3; ++s) {
+    beta[0][0][s] = uu[s];
+    beta[1][1][s] = uu[s];
+    beta[0][1][s] = adjoint ? vu[s] : uv[s];
+    beta[1][0][s] = adjoint ? uv[s] : vu[s];
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int q = 0; q < 16; ++q) {
+      out->gx[a][q] = GR[0][a][q];
+      out->gy[a][q] = GR[1][a][q];
+    }
+  for (int fo = 0; fo < 2; ++fo)
+    for (int fi = 0; fi < 2; ++fi)
+      for (int g = 0; g < 3; ++g)
+        for (int q = 0; q < 16; ++q) {
+          double v = 0.0;
+          for (int cz = 0; cz + g <= 2; ++cz) v += beta[fo][fi][g + cz] * GR[2][cz][q];
+          out->kz[fo][fi][g][q] = v;
+        }
+}
+
+}  // namespace hermite

@@ -1,0 +1,124 @@
+"""Python front end of libhermite (argument marshalling only).
+
+Device states are torch tensors (torch provides device memory and the current
+CUDA stream); host states are numpy arrays or CPU tensors.  Every arithmetic
+step of the half step runs in the CUDA library.
+"""
+import ctypes
+
+import numpy as np
+
+from . import capi
+
+PRECISIONS = {"fp64": capi.HERMITE_FP64, "fp32": capi.HERMITE_FP32}
+STATES = {"fp64": capi.HERMITE_STATE_FP64, "fp32": capi.HERMITE_STATE_FP32}
+VARIANTS = {"auto": capi.HERMITE_AUTO, "fused": capi.HERMITE_FUSED, "split": capi.HERMITE_SPLIT}
+
+
+def stability_limit(m):
+    """Largest c*(dt/2)/h with a stable half step of order m."""
+    return capi.lib.hermite_stability_limit(int(m))
+
+
+def _ptr(x):
+    """(address, is_device) of a contiguous torch tensor or numpy array."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("state arrays must be C-contiguous")
+        return x.ctypes.data, False
+    if not x.is_contiguous():
+        raise ValueError("state tensors must be contiguous")
+    return x.data_ptr(), x.is_cuda
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """A half-step plan: order m, periodic grid (n1, n2, n3), spacings h, wave
+    speed c and FULL time step dt (each step advances dt / 2)."""
+
+    def __init__(self, m, grid, h, c, dt, prec="fp64", state="fp64", variant="auto"):
+        self.m, self.grid, self.h = int(m), tuple(int(v) for v in grid), tuple(float(v) for v in h)
+        self.c, self.dt, self.prec, self.state, self.variant = float(c), float(dt), prec, state, variant
+        handle = ctypes.c_void_p()
+        capi.check(capi.lib.hermite_plan(ctypes.byref(handle), self.m, (ctypes.c_int * 3)(*self.grid),
+                                         (ctypes.c_double * 3)(*self.h), self.c, self.dt,
+                                         PRECISIONS[prec], STATES[state], VARIANTS[variant]))
+        self._h = handle
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    @property
+    def shape(self):
+        M = self.m + 1
+        return (2, M, M, M, self.grid[2], self.grid[1], self.grid[0])
+
+    @property
+    def elems(self):
+        return capi.lib.hermite_state_elems(self.handle)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.state == "fp64" else torch.float32
+
+    def empty(self, device="cuda"):
+        import torch
+        return torch.empty(self.shape, dtype=self.torch_dtype, device=device)
+
+    def operator(self):
+        P = 2 * self.m + 2
+        out = (ctypes.c_double * (P * P))()
+        capi.check(capi.lib.hermite_plan_operator(self.handle, out))
+        return np.array(out).reshape(P, P)
+
+    def _check(self, *xs):
+        for x in xs:
+            if tuple(x.shape) != self.shape:
+                raise ValueError(f"state shape {tuple(x.shape)} != {self.shape}")
+
+    def step(self, x_in, x_out, parity, stream=None):
+        """x_out = S_parity(x_in) (device tensors: enqueued; host arrays: synchronous)."""
+        self._check(x_in, x_out)
+        pi, di = _ptr(x_in)
+        po, do = _ptr(x_out)
+        st = _stream(stream) if (di or do) else ctypes.c_void_p(int(stream or 0))
+        capi.check(capi.lib.hermite_step(self.handle, ctypes.c_void_p(pi), ctypes.c_void_p(po), int(parity), st))
+        return x_out
+
+    def adjoint(self, g_out, g_in, parity, stream=None):
+        """g_in = S_parity^T g_out (device tensors)."""
+        self._check(g_out, g_in)
+        capi.check(capi.lib.hermite_adjoint_step(self.handle, ctypes.c_void_p(_ptr(g_out)[0]),
+                                                 ctypes.c_void_p(_ptr(g_in)[0]), int(parity), _stream(stream)))
+        return g_in
+
+    def error(self, x, ref, mask=0b111, stream=None):
+        """(max_abs, max_rel, rms, l2_rel) of x - ref (ref FP64, device tensors)."""
+        self._check(x, ref)
+        out = (ctypes.c_double * 4)()
+        rc = capi.lib.hermite_error(self.handle, ctypes.c_void_p(_ptr(x)[0]), ctypes.c_void_p(_ptr(ref)[0]),
+                                    int(mask), out, _stream(stream))
+        if rc not in (capi.HERMITE_OK, capi.HERMITE_ENONFINITE):
+            capi.check(rc)
+        return tuple(out), rc
+
+    def close(self):
+        if self._h is not None:
+            capi.lib.hermite_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

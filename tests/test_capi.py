@@ -1,0 +1,107 @@
+"""Host-side tests of the C ABI (no GPU needed): the library loads, exports
+every entry point declared in include/*.h, validates plans, and its exact
+rational tables agree with the oracle's."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import hermite as oracle_hermite
+from oracle import symbol
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1609_09841_gb300 import capi as c
+    return c
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+        for mt in re.finditer(r"\b(hermite_[a-z0-9_]+)\s*\(", src):
+            names.add(mt.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(capi):
+    names = _declared_functions()
+    assert "hermite_step" in names and "hermite_plan" in names
+    for name in sorted(names):
+        assert hasattr(capi.lib, name), name
+
+
+def _plan(capi, m=1, grid=(8, 8, 8), h=None, c=1.0, dt=None, prec=0, state=0, variant=0):
+    h = h or tuple(1.0 / max(g, 1) for g in grid)
+    dt = dt if dt is not None else 0.4 * min(h)
+    p = ctypes.c_void_p()
+    rc = capi.lib.hermite_plan(ctypes.byref(p), m, (ctypes.c_int * 3)(*grid), (ctypes.c_double * 3)(*h),
+                               c, dt, prec, state, variant)
+    return rc, p
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(m=0), -1), (dict(m=4), -1), (dict(grid=(0, 4, 4)), -1), (dict(h=(0.1, -0.1, 0.1)), -1),
+    (dict(c=0.0), -1), (dict(dt=0.0), -1), (dict(prec=7), -4), (dict(state=5), -1),
+    (dict(prec=0, state=1), -4), (dict(variant=9), -1), (dict(dt=1.0), -5),
+])
+def test_plan_rejects_bad_arguments(capi, kw, code):
+    rc, p = _plan(capi, **kw)
+    assert rc == code, capi.last_error()
+    assert not p.value
+    assert capi.last_error()
+
+
+def test_plan_accepts_and_reports_sizes(capi):
+    rc, p = _plan(capi, m=2, grid=(5, 6, 7))
+    assert rc == 0
+    assert capi.lib.hermite_state_elems(p) == 2 * 27 * 5 * 6 * 7
+    capi.lib.hermite_destroy(p)
+    capi.lib.hermite_destroy(None)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_library_H_equals_oracle_exact_H(capi, m):
+    rc, p = _plan(capi, m=m)
+    assert rc == 0
+    P = 2 * m + 2
+    buf = (ctypes.c_double * (P * P))()
+    assert capi.lib.hermite_plan_operator(p, buf) == 0
+    capi.lib.hermite_destroy(p)
+    ref = np.array([[float(v) for v in row] for row in oracle_hermite.hermite_matrix_exact(m)])
+    assert np.array_equal(np.array(buf).reshape(P, P), ref)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_stability_table_agrees_with_symbol(capi, m):
+    """The library's limit is stable by the oracle's symbol, 4% above it is
+    not, and plans straddling it are accepted / rejected."""
+    lim = capi.lib.hermite_stability_limit(m)
+    assert symbol.max_spectral_radius(m, lim, npts=7) <= 1.0 + 1e-10
+    assert symbol.max_spectral_radius(m, lim * 1.04, npts=9) > 1.0 + 1e-9
+    h = 1.0 / 16
+    assert _plan(capi, m=m, grid=(16,) * 3, dt=2 * lim * h * 0.999)[0] == 0
+    assert _plan(capi, m=m, grid=(16,) * 3, dt=2 * lim * h * 1.01)[0] == -5
+
+
+def test_step_without_gpu_fails_cleanly(capi):
+    """On a machine without a CUDA device the step reports an error code
+    instead of crashing (skipped when a GPU is present)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, p = _plan(capi)
+    assert rc == 0
+    a = np.zeros(capi.lib.hermite_state_elems(p))
+    b = np.zeros_like(a)
+    rc = capi.lib.hermite_step(p, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p), 0, None)
+    assert rc < 0
+    capi.lib.hermite_destroy(p)

@@ -1,0 +1,229 @@
+"""GPU parity of the CUDA half step (through the C ABI) against the FP64 oracle.
+
+FP64: relative max-norm difference <= 1e-12 (the stated FP64 bar).
+FP32 arithmetic: see fp32_bound below for the tolerance and its derivation.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import hermite_inputs as HI
+from oracle import hermite as oracle
+
+pytestmark = pytest.mark.gpu
+
+# Grids span several CTA tiles (8x8 for m=1, 4x4 otherwise in FP64) with
+# ragged tails in x and y, and z-chunks with a partial last chunk.
+GRIDS = {1: (19, 13, 11), 2: (9, 7, 6), 3: (9, 6, 5)}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def _plan(m, n, prec="fp64", state="fp64", variant="auto", c=1.0, lam=0.2):
+    from paper_1609_09841_gb300 import Plan
+    h = tuple(1.0 / v for v in n)
+    dt = 2 * lam * min(h) / c
+    return Plan(m, n, h, c, dt, prec=prec, state=state, variant=variant), h, dt
+
+
+def _relmax(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("variant", ["fused", "split"])
+def test_fp64_step_matches_oracle(torch_cuda, m, parity, variant):
+    torch = torch_cuda
+    n = GRIDS[m]
+    plan, h, dt = _plan(m, n, variant=variant, c=1.3)
+    x = HI.random_state(m, n, seed=10 + m)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    plan.step(xd, yd, parity)
+    ref = oracle.half_step(x, m, h, 1.3, dt, parity)
+    assert _relmax(yd.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("parity", [0, 1])
+def test_fp64_adjoint_matches_oracle(torch_cuda, m, parity):
+    torch = torch_cuda
+    n = GRIDS[m]
+    plan, h, dt = _plan(m, n, c=0.8)
+    g = HI.random_state(m, n, seed=20 + m)
+    gd = torch.from_numpy(g).cuda()
+    out = torch.full_like(gd, float("nan"))
+    plan.adjoint(gd, out, parity)
+    ref = oracle.adjoint_half_step(g, m, h, 0.8, dt, parity)
+    assert _relmax(out.cpu().numpy(), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [(1, 1, 1), (2, 2, 2), (1, 3, 2), (17, 1, 4)])
+@pytest.mark.parametrize("m", [1, 3])
+def test_degenerate_grids(torch_cuda, n, m):
+    """Grids thinner than a tile, including a single node per dimension
+    (every corner of a cell is the same node)."""
+    torch = torch_cuda
+    plan, h, dt = _plan(m, n)
+    x = HI.random_state(m, n, seed=3)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    for parity in (0, 1):
+        plan.step(xd, yd, parity)
+        ref = oracle.half_step(x, m, h, 1.0, dt, parity)
+        assert _relmax(yd.cpu().numpy(), ref) <= 1e-12
+
+
+def test_gpu_dot_product_identity(torch_cuda):
+    torch = torch_cuda
+    m, n = 2, (32, 24, 20)
+    plan, h, dt = _plan(m, n)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(plan.shape, dtype=torch.float64, device="cuda", generator=gen)
+    y = torch.randn(plan.shape, dtype=torch.float64, device="cuda", generator=gen)
+    sx, sty = torch.empty_like(x), torch.empty_like(x)
+    for parity in (0, 1):
+        plan.step(x, sx, parity)
+        plan.adjoint(y, sty, parity)
+        lhs, rhs = float((sx * y).sum()), float((x * sty).sum())
+        assert abs(lhs - rhs) <= 1e-13 * float(sx.norm() * y.norm())
+
+
+def test_host_buffer_step_equals_device_step(torch_cuda):
+    torch = torch_cuda
+    m, n = 2, (9, 8, 7)
+    for state in ("fp64", "fp32"):
+        plan, h, dt = _plan(m, n, prec="fp32" if state == "fp32" else "fp64", state=state)
+        x = HI.random_state(m, n, seed=8).astype(np.float64 if state == "fp64" else np.float32)
+        y_host = np.empty_like(x)
+        plan.step(x, y_host, 1)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        plan.step(xd, yd, 1)
+        assert np.array_equal(y_host, yd.cpu().numpy())
+
+
+def test_invalid_buffers_rejected(torch_cuda):
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import capi
+    plan, h, dt = _plan(1, (8, 8, 8))
+    x = plan.empty()
+    with pytest.raises(capi.HermiteError) as e:
+        plan.step(x, x, 0)
+    assert e.value.code == capi.HERMITE_EINVAL
+    big = torch.empty(plan.elems * 2 + 1, dtype=torch.float64, device="cuda")
+    rc = capi.lib.hermite_step(plan.handle, ctypes.c_void_p(big.data_ptr() + 8),
+                               ctypes.c_void_p(big.data_ptr() + 8 * (plan.elems + 1)), 0, None)
+    assert rc == capi.HERMITE_EINVAL
+    rc = capi.lib.hermite_step(plan.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(big.data_ptr()), 2, None)
+    assert rc == capi.HERMITE_EINVAL
+
+
+def fp32_bound(m, n, h, c, dt, parity, x):
+    """Elementwise tolerance of an FP32-arithmetic half step.
+
+    Each output is a sum of products; computing it in FP32 from FP32 data
+    errs by at most about k * eps32 * (|W| |x|)_i, with W the half step's
+    per-cell matrix and k the number of rounding steps along the longest
+    chain of the factorised evaluation (x-, y- and z-passes, butterflies,
+    input rounding): k <= 48 for m <= 3.  The factorised evaluation can have
+    larger intermediate sums than |W| |x| (|Gz||Gy||Gx| >= |W| entrywise), so
+    the bound uses the absolute value of each 1-D factor: it is the oracle's
+    half step with every corner block replaced by its absolute value, which
+    majorises both."""
+    M = m + 1
+    eps32 = 2.0 ** -24
+    s = 0 if parity == 0 else -1
+    W = oracle.cell_matrix(m, h, c, dt)
+    blocks = oracle.corner_blocks(np.abs(W), m)
+    X = np.abs(x).reshape((2 * M ** 3,) + x.shape[-3:])
+    acc = np.zeros((2 * M ** 3, X[0].size))
+    for (a, b, cc), Wb in blocks.items():
+        sh = np.roll(X, shift=(-(s + cc), -(s + b), -(s + a)), axis=(1, 2, 3))
+        acc += Wb @ sh.reshape(2 * M ** 3, -1)
+    return 48 * eps32 * acc.reshape(x.shape)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("state", ["fp32", "fp64"])
+def test_fp32_step_within_rounding_bound(torch_cuda, m, state):
+    torch = torch_cuda
+    n = GRIDS[m]
+    plan, h, dt = _plan(m, n, prec="fp32", state=state)
+    x = HI.random_state(m, n, seed=30 + m)
+    if state == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x).cuda().to(plan.torch_dtype)
+    yd = torch.empty_like(xd)
+    for parity in (0, 1):
+        plan.step(xd, yd, parity)
+        ref = oracle.half_step(x, m, h, 1.0, dt, parity)
+        bound = fp32_bound(m, n, h, 1.0, dt, parity, x)
+        err = np.abs(yd.cpu().numpy().astype(np.float64) - ref)
+        assert np.all(err <= bound + 1e-30), float(np.max(err / (bound + 1e-30)))
+        assert _relmax(yd.cpu().numpy().astype(np.float64), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("state", ["fp64", "fp32"])
+@pytest.mark.parametrize("mask", [0b001, 0b010, 0b011, 0b111, 0b101])
+def test_error_norms_match_oracle(torch_cuda, state, mask):
+    torch = torch_cuda
+    m, n = 2, (13, 9, 11)
+    plan, h, dt = _plan(m, n, prec="fp32" if state == "fp32" else "fp64", state=state)
+    a = HI.random_state(m, n, seed=40)
+    b = HI.random_state(m, n, seed=41)
+    if state == "fp32":
+        a = a.astype(np.float32).astype(np.float64)
+    (vals, rc) = plan.error(torch.from_numpy(a).cuda().to(plan.torch_dtype), torch.from_numpy(b).cuda(), mask)
+    assert rc == 0
+    ref = oracle.error_norms(a, b, mask)
+    assert np.allclose(vals, ref, rtol=1e-12, atol=0)
+
+
+def test_error_norms_flag_nonfinite(torch_cuda):
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import capi
+    plan, h, dt = _plan(1, (8, 8, 8))
+    a = torch.zeros(plan.shape, dtype=torch.float64, device="cuda")
+    b = torch.ones_like(a)
+    a[1, 1, 0, 1, 3, 2, 1] = float("nan")
+    vals, rc = plan.error(a, b, 0b111)
+    assert rc == capi.HERMITE_ENONFINITE
+    vals, rc = plan.error(a, b, 0b001)   # the NaN is in v's derivatives: not selected
+    assert rc == 0
+
+
+def test_standing_mode_config1_matches_oracle(torch_cuda):
+    """16^3, m = 1, dt = 0.5 h, 100 half steps of the product standing mode:
+    GPU FP64 (fused and split) vs the oracle's run, and both vs the closed
+    form."""
+    torch = torch_cuda
+    from oracle import exact
+    m, n = 1, (16, 16, 16)
+    h = (1 / 16,) * 3
+    dt = 0.5 * h[0]
+    x0 = HI.product_standing_mode(m, n, h)
+    ref = oracle.run(x0, m, h, 1.0, dt, 100)
+    closed = exact.product_mode(m, n, h, 1.0, 100 * dt / 2)
+    from paper_1609_09841_gb300 import Plan
+    for variant in ("fused", "split"):
+        plan = Plan(m, n, h, 1.0, dt, variant=variant)
+        a = torch.from_numpy(x0).cuda()
+        b = torch.empty_like(a)
+        for k in range(100):
+            plan.step(a, b, k % 2)
+            a, b = b, a
+        out = a.cpu().numpy()
+        assert _relmax(out, ref) <= 1e-12
+        vals, rc = plan.error(a, torch.from_numpy(closed).cuda(), 0b001)
+        assert abs(vals[0] - oracle.error_norms(ref, closed, 0b001)[0]) <= 1e-12
