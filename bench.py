@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (profiling runs use a smaller one)")
+    ap.add_argument("--m", type=int, default=M_ORDER)
+    ap.add_argument("--legs", default="mixed,mixed64,fp64,e2e",
+                    help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), fp64, e2e")
     return ap.parse_args()
 
 
@@ -134,16 +138,18 @@ def run_ours(args, rank, world):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1609_09841_gb300 import Plan
+    from paper_1609_09841_gb300.autotune import tune
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    m, n = M_ORDER, (N_SIDE,) * 3
-    h = (1.0 / N_SIDE,) * 3
+    m, n = args.m, (args.side,) * 3
+    h = (1.0 / args.side,) * 3
     dt = 0.4 * h[0]
-    dof = dof_per_step()
+    dof = dof_per_step(m, args.side)
+    legs = set(args.legs.split(","))
     gen = torch.Generator(device="cuda").manual_seed(1609 + rank)
 
     def barrier():
@@ -162,6 +168,8 @@ def run_ours(args, rank, world):
     plan = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp32")
     x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
     y = torch.empty_like(x)
+    sched = {"mixed": tune(plan, x, y, cache=None)}
+    x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
     for k in range(args.warmup):
         plan.step(x, y, k % 2)
         x, y = y, x
@@ -178,25 +186,30 @@ def run_ours(args, rank, world):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = traffic_alg / (ms * 1e-3) / 1e9
-    # same arithmetic, FP64 state (loaded, computed in FP32, stored)
-    plan64s = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp64")
-    xd = x.double()
-    yd = torch.empty_like(xd)
-    ms_mixed64 = timed_steps(torch, plan64s, xd, yd, args.steps, args.warmup)
-    # plain FP64
-    plan64 = Plan(m, n, h, 1.0, dt, prec="fp64", state="fp64")
-    ms64 = timed_steps(torch, plan64, xd, yd, args.fp64_steps, min(args.warmup, 3))
-    del xd, yd
-    # end to end through the C ABI with pinned host buffers (FP32 state)
-    hx = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
-    hy = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
-    hx.copy_(x)
-    plan.step(hx.numpy(), hy.numpy(), 0)
-    t0 = time.perf_counter()
-    for k in range(args.e2e_steps):
-        plan.step(hx.numpy(), hy.numpy(), k % 2)
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_s = max_over_ranks(e2e_s)
+    ms_mixed64 = ms64 = e2e_s = float("nan")
+    if legs & {"mixed64", "fp64"}:
+        xd = x.double()
+        yd = torch.empty_like(xd)
+        if "mixed64" in legs:   # same arithmetic, FP64 state (loaded, computed in FP32, stored)
+            plan64s = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp64")
+            sched["mixed64"] = tune(plan64s, xd, yd, cache=None)
+            xd.copy_(x)
+            ms_mixed64 = timed_steps(torch, plan64s, xd, yd, args.steps, args.warmup)
+        if "fp64" in legs:      # plain FP64
+            plan64 = Plan(m, n, h, 1.0, dt, prec="fp64", state="fp64")
+            sched["fp64"] = tune(plan64, xd, yd, zchunks=(16, 32), reps=1, cache=None)
+            xd.copy_(x)
+            ms64 = timed_steps(torch, plan64, xd, yd, args.fp64_steps, min(args.warmup, 3))
+        del xd, yd
+    if "e2e" in legs:           # end to end through the C ABI with pinned host buffers (FP32 state)
+        hx = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
+        hy = torch.empty(plan.shape, dtype=torch.float32, pin_memory=True)
+        hx.copy_(x)
+        plan.step(hx.numpy(), hy.numpy(), 0)
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            plan.step(hx.numpy(), hy.numpy(), k % 2)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps)
     bytes_state = plan.elems * 4
     out = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
@@ -217,6 +230,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * dof / e2e_s, "unit": "DOF-updates/s", "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state, "seconds_per_step": e2e_s},
         "gpu_launches": args.steps,
+        "schedule": {k: {"tile": v["tile"], "zchunk": v["zchunk"], "ms": v["ms"]} for k, v in sched.items()},
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -253,17 +267,26 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _clean(v):
+    """JSON without NaN: legs that were not run report null."""
+    if isinstance(v, dict):
+        return {k: _clean(x) for k, x in v.items()}
+    if isinstance(v, float) and not np.isfinite(v):
+        return None
+    return v
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args)))
+            print(json.dumps(_clean(run_reference(args))))
         return
     out = run_ours(args, rank, world)
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(_clean(out)))
 
 
 if __name__ == "__main__":

@@ -38,7 +38,7 @@
  *               i is the centre of the cell with dual corners i-1, i).
  *   stream      a cudaStream_t cast to void* (NULL = the legacy default stream).
  *               All work is enqueued on it and the calls return without waiting,
- *               except hermite_error, hermite_last_status and host-buffer steps.
+ *               except hermite_error, hermite_dot and host-buffer steps.
  *
  * Errors: every int-returning call returns HERMITE_OK (0) or a negative
  * hermite_status; hermite_last_error() then describes the failure (a
@@ -115,6 +115,37 @@ int hermite_adjoint_step(hermite_plan_t plan, const void *out_adj, void *in_adj,
  * (with out filled) if any selected entry of either array is NaN or Inf. */
 int hermite_error(hermite_plan_t plan, const void *state, const void *ref, unsigned component_mask,
                   double out[4], void *stream);
+
+/* Derivative of the half step with respect to the wave speed:
+ * out = (dS_parity / dc) in.  Every term of the half step's Taylor series of
+ * order s in the Laplacian (Alg. 4) scales as c^(2s), so dS/dc is the same
+ * operator with that term weighted by 2s/c.  Used to assemble gradients with
+ * respect to c from forward states (recomputed from checkpoints) and adjoint
+ * states.  Device buffers only; same rules as hermite_step. */
+int hermite_step_dc(hermite_plan_t plan, const void *in_state, void *out_state, int parity,
+                    void *stream);
+
+/* FP64 dot product sum_i a_i b_i of two device states of the plan's state
+ * type (all 2 M^3 n1 n2 n3 entries).  Synchronises `stream`. */
+int hermite_dot(hermite_plan_t plan, const void *a, const void *b, double *out, void *stream);
+
+/* Receivers.  idx (device, count entries) holds flat node indices
+ * z*n1*n2 + y*n1 + x.  hermite_record writes out[k] (device, FP64) = the value
+ * of u (orders (0,0,0)) at node idx[k] of `state`; hermite_inject adds w[k]
+ * (device, FP64) to the same entries of an adjoint state (its transpose;
+ * repeated indices accumulate).  Both only enqueue work on `stream`. */
+int hermite_record(hermite_plan_t plan, const void *state, const long long *idx, int count,
+                   double *out, void *stream);
+int hermite_inject(hermite_plan_t plan, void *adj_state, const long long *idx, int count,
+                   const double *w, void *stream);
+
+/* Kernel schedule of the fused half step: `tile` picks one of
+ * hermite_schedule_count(plan) compiled tile shapes (cells per CTA in x1, x2
+ * and threads per CTA, fixed per order and precision), `zchunk` the cells
+ * each CTA marches along x3 (1..4096).  Defaults: tile 0, zchunk 16.  The
+ * autotuner of the Python package times the choices on the device. */
+int hermite_schedule_count(hermite_plan_t plan);
+int hermite_set_schedule(hermite_plan_t plan, int tile, int zchunk);
 
 /* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
 size_t hermite_state_elems(hermite_plan_t plan);

@@ -51,6 +51,12 @@ def _load():
         "hermite_stability_limit": (D, [I]),
         "hermite_plan_operator": (I, [P, DP]),
         "hermite_destroy": (None, [P]),
+        "hermite_step_dc": (I, [P, P, P, I, P]),
+        "hermite_schedule_count": (I, [P]),
+        "hermite_set_schedule": (I, [P, I, I]),
+        "hermite_dot": (I, [P, P, P, DP, P]),
+        "hermite_record": (I, [P, P, P, I, P, P]),
+        "hermite_inject": (I, [P, P, P, I, P, P]),
         "hermite_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

@@ -24,10 +24,11 @@ struct hermite_plan_s {
   int prec, state, variant;
   size_t elems;
   double H[64];
-  StepCoeffs<double> fwd, adj;
-  StepCoeffs<float> fwd32, adj32;
+  StepCoeffs<double> fwd, adj, dc;
+  StepCoeffs<float> fwd32, adj32, dc32;
   InterpCoeffs<double> interp;
   EvolveParams evolve;
+  int tile;                 // fused kernel: index of the compiled tile shape
   int zchunk;               // fused kernel: cells per CTA along x3
   size_t ws_limit;          // split variant: workspace budget in bytes
   void *ws = nullptr;       // split workspace (device), grown on demand
@@ -114,20 +115,45 @@ int ensure_ws(hermite_plan_s *p, size_t bytes) {
   return HERMITE_OK;
 }
 
+// Reduction scratch: (error_blocks() + 1) * 8 doubles on the device (result
+// first, then the per-CTA partials) and an 8-double pinned result buffer.
+int ensure_red(hermite_plan_s *p) {
+  if (p->red && p->red_host) return HERMITE_OK;
+  if (!p->red) {
+    cudaError_t e = cudaMalloc(&p->red, sizeof(double) * (size_t)(error_blocks() + 1) * 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->red = nullptr;
+      return fail(HERMITE_ENOMEM, "reduction scratch");
+    }
+  }
+  cudaError_t e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->red_host = nullptr;
+    return fail(HERMITE_ENOMEM, "pinned result buffer");
+  }
+  return HERMITE_OK;
+}
+
 // Device-pointer half step of either direction (adjoint: transposed tables,
 // mirrored corner offset).
-int run_step(hermite_plan_s *p, const void *in, void *out, int parity, bool adjoint, cudaStream_t st) {
+int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st) {
   const int s_fwd = parity == 0 ? 0 : -1;
+  const bool adjoint = mode == kAdjoint;
   const int s = adjoint ? -s_fwd - 1 : s_fwd;
   const Geom g = geom_of(p, s);
-  const bool split = p->variant == HERMITE_SPLIT && !adjoint;
+  const bool split = p->variant == HERMITE_SPLIT && mode == kForward;
   cudaError_t e = cudaSuccess;
   if (!split) {
+    const StepCoeffs<double> &cd = mode == kAdjoint ? p->adj : (mode == kDc ? p->dc : p->fwd);
+    const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
     if (p->prec == HERMITE_FP64)
-      e = launch_fused_f64(p->m, (const double *)in, (double *)out, g, adjoint ? p->adj : p->fwd, p->zchunk, st);
+      e = launch_fused_f64(p->m, p->tile, (const double *)in, (double *)out, g, cd, p->zchunk, st);
+    else if (p->state == HERMITE_STATE_FP64)
+      e = launch_fused_f32_s64(p->m, p->tile, (const double *)in, (double *)out, g, cf, p->zchunk, st);
     else
-      e = launch_fused_f32(p->m, p->state == HERMITE_STATE_FP64 ? kF64 : kF32, in, out, g,
-                           adjoint ? p->adj32 : p->fwd32, p->zchunk, st);
+      e = launch_fused_f32_s32(p->m, p->tile, (const float *)in, (float *)out, g, cf, p->zchunk, st);
     if (e != cudaSuccess) return cuda_fail(e, "fused half-step launch");
     return HERMITE_OK;
   }
@@ -201,13 +227,16 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   p->variant = variant == HERMITE_AUTO ? HERMITE_FUSED : variant;
   p->elems = (size_t)2 * (m + 1) * (m + 1) * (m + 1) * nodes;
   build_H(m, p->H);
-  build_step_coeffs(m, h, c, tau, false, &p->fwd);
-  build_step_coeffs(m, h, c, tau, true, &p->adj);
+  build_step_coeffs(m, h, c, tau, kForward, &p->fwd);
+  build_step_coeffs(m, h, c, tau, kAdjoint, &p->adj);
+  build_step_coeffs(m, h, c, tau, kDc, &p->dc);
   p->fwd32 = cast_coeffs<float>(p->fwd);
   p->adj32 = cast_coeffs<float>(p->adj);
+  p->dc32 = cast_coeffs<float>(p->dc);
   build_interp_coeffs(m, &p->interp);
   p->evolve.tau = tau;
   for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
+  p->tile = 0;
   p->zchunk = 16;
   p->ws_limit = (size_t)1 << 30;
   *out = p;
@@ -215,6 +244,17 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
 }
 
 size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
+
+int hermite_schedule_count(hermite_plan_t p) { return p ? fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m) : 0; }
+
+int hermite_set_schedule(hermite_plan_t p, int tile, int zchunk) {
+  if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (tile < 0 || tile >= hermite_schedule_count(p)) return fail(HERMITE_EINVAL, "tile %d out of range", tile);
+  if (zchunk < 1 || zchunk > 4096) return fail(HERMITE_EINVAL, "zchunk %d out of range", zchunk);
+  p->tile = tile;
+  p->zchunk = zchunk;
+  return HERMITE_OK;
+}
 
 int hermite_plan_operator(hermite_plan_t p, double *out) {
   if (!p || !out) return fail(HERMITE_EINVAL, "null argument");
@@ -234,7 +274,7 @@ int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *
   if (ki == kDevicePtr) {
     int rc = check_device_pair(p, in, out);
     if (rc) return rc;
-    return run_step(p, in, out, parity, false, st);
+    return run_step(p, in, out, parity, kForward, st);
   }
   // Host buffers: copy in, step, copy out through plan-owned device buffers.
   const size_t bytes = state_bytes(p);
@@ -250,7 +290,7 @@ int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *
     }
   cudaError_t e = cudaMemcpyAsync(p->stage[0], in, bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-  int rc = run_step(p, p->stage[0], p->stage[1], parity, false, st);
+  int rc = run_step(p, p->stage[0], p->stage[1], parity, kForward, st);
   if (rc) return rc;
   e = cudaMemcpyAsync(out, p->stage[1], bytes, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
@@ -266,7 +306,36 @@ int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, in
   if (rc) return rc;
   if (classify(out_adj) != kDevicePtr || classify(in_adj) != kDevicePtr)
     return fail(HERMITE_EINVAL, "adjoint steps take device buffers");
-  return run_step(p, out_adj, in_adj, parity, true, (cudaStream_t)stream);
+  return run_step(p, out_adj, in_adj, parity, kAdjoint, (cudaStream_t)stream);
+}
+
+int hermite_step_dc(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
+  if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
+  int rc = check_device_pair(p, in, out);
+  if (rc) return rc;
+  if (classify(in) != kDevicePtr || classify(out) != kDevicePtr)
+    return fail(HERMITE_EINVAL, "hermite_step_dc takes device buffers");
+  return run_step(p, in, out, parity, kDc, (cudaStream_t)stream);
+}
+
+int hermite_record(hermite_plan_t p, const void *state, const long long *idx, int count, double *out,
+                   void *stream) {
+  if (!p || !state || !idx || !out) return fail(HERMITE_EINVAL, "null argument");
+  if (count < 0) return fail(HERMITE_EINVAL, "negative receiver count");
+  if (count == 0) return HERMITE_OK;
+  cudaError_t e = launch_record(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, state, idx, count, out,
+                                (cudaStream_t)stream);
+  return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "record launch");
+}
+
+int hermite_inject(hermite_plan_t p, void *adj, const long long *idx, int count, const double *w, void *stream) {
+  if (!p || !adj || !idx || !w) return fail(HERMITE_EINVAL, "null argument");
+  if (count < 0) return fail(HERMITE_EINVAL, "negative receiver count");
+  if (count == 0) return HERMITE_OK;
+  cudaError_t e = launch_inject(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, adj, idx, count, w,
+                                (cudaStream_t)stream);
+  return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "inject launch");
 }
 
 int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned mask, double out[4],
@@ -277,20 +346,8 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
     return fail(HERMITE_EINVAL, "hermite_error takes device buffers");
   cudaStream_t st = (cudaStream_t)stream;
   const int blocks = error_blocks();
-  if (!p->red) {
-    cudaError_t e = cudaMalloc(&p->red, sizeof(double) * (size_t)(blocks + 1) * 8);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p->red = nullptr;
-      return fail(HERMITE_ENOMEM, "reduction scratch");
-    }
-    e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      p->red_host = nullptr;
-      return fail(HERMITE_ENOMEM, "pinned result buffer");
-    }
-  }
+  int rc = ensure_red(p);
+  if (rc) return rc;
   const size_t plane = (size_t)p->n[0] * p->n[1] * p->n[2];
   cudaError_t e = launch_error(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, state, (const double *)ref, p->m,
                                plane, mask, p->red + 8, blocks, p->red, st);
@@ -307,6 +364,23 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
   out[2] = std::sqrt(r[2] / count);
   out[3] = r[3] > 0 ? std::sqrt(r[2] / r[3]) : INFINITY;
   if (r[4] > 0) return fail(HERMITE_ENONFINITE, "%.0f non-finite entries", r[4]);
+  return HERMITE_OK;
+}
+
+int hermite_dot(hermite_plan_t p, const void *a, const void *b, double *out, void *stream) {
+  if (!p || !a || !b || !out) return fail(HERMITE_EINVAL, "null argument");
+  if (classify(a) != kDevicePtr || classify(b) != kDevicePtr) return fail(HERMITE_EINVAL, "hermite_dot takes device buffers");
+  int rc = ensure_red(p);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_dot(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, a, b, p->elems, p->red + 8,
+                             error_blocks(), p->red, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dot launch");
+  e = cudaMemcpyAsync(p->red_host, p->red, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dot copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+  *out = p->red_host[2];
   return HERMITE_OK;
 }
 

@@ -1,0 +1,28 @@
+// Tile shapes of the FP32-arithmetic fused kernel, per order m.
+#pragma once
+
+#include "fused.cuh"
+
+namespace hermite {
+
+template <typename TS>
+cudaError_t dispatch_f32(int m, int tile, const TS *in, TS *out, const Geom &g, const StepCoeffs<float> &co,
+                         int zchunk, cudaStream_t st) {
+  switch (m * 8 + tile) {
+    case 8 + 0: return launch_fused_cfg<TS, float, 2, 16, 8, 512>(in, out, g, co, zchunk, st);
+    case 8 + 1: return launch_fused_cfg<TS, float, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
+    case 8 + 2: return launch_fused_cfg<TS, float, 2, 32, 4, 512>(in, out, g, co, zchunk, st);
+    case 8 + 3: return launch_fused_cfg<TS, float, 2, 16, 16, 1024>(in, out, g, co, zchunk, st);
+    case 16 + 0: return launch_fused_cfg<TS, float, 3, 8, 4, 288>(in, out, g, co, zchunk, st);
+    case 16 + 1: return launch_fused_cfg<TS, float, 3, 4, 4, 160>(in, out, g, co, zchunk, st);
+    case 16 + 2: return launch_fused_cfg<TS, float, 3, 8, 8, 576>(in, out, g, co, zchunk, st);
+    case 16 + 3: return launch_fused_cfg<TS, float, 3, 16, 4, 576>(in, out, g, co, zchunk, st);
+    case 24 + 0: return launch_fused_cfg<TS, float, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
+    case 24 + 1: return launch_fused_cfg<TS, float, 4, 8, 4, 256>(in, out, g, co, zchunk, st);
+    case 24 + 2: return launch_fused_cfg<TS, float, 4, 8, 4, 512>(in, out, g, co, zchunk, st);
+    case 24 + 3: return launch_fused_cfg<TS, float, 4, 4, 2, 128>(in, out, g, co, zchunk, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hermite

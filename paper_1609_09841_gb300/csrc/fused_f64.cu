@@ -1,15 +1,29 @@
 // FP64 instantiations of the fused half-step kernel (state and arithmetic in
-// double; used for the plain method and its discrete adjoint).
+// double; used for the plain method, its adjoint and dS/dc).  Each order has
+// a few tile shapes (TX x TY cells per CTA, threads); the plan's schedule
+// picks one (see the autotuner).
 #include "fused.cuh"
 
 namespace hermite {
 
-cudaError_t launch_fused_f64(int m, const double *in, double *out, const Geom &g,
+int fused_tile_count(int prec, int m) {
+  (void)m;
+  return prec == 0 ? 3 : 4;
+}
+
+cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,
                              const StepCoeffs<double> &co, int zchunk, cudaStream_t st) {
-  switch (m) {
-    case 1: return launch_fused_cfg<double, double, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
-    case 2: return launch_fused_cfg<double, double, 3, 4, 4, 160>(in, out, g, co, zchunk, st);
-    case 3: return launch_fused_cfg<double, double, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
+  using T = double;
+  switch (m * 8 + tile) {
+    case 8 + 0: return launch_fused_cfg<T, T, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
+    case 8 + 1: return launch_fused_cfg<T, T, 2, 16, 4, 256>(in, out, g, co, zchunk, st);
+    case 8 + 2: return launch_fused_cfg<T, T, 2, 16, 8, 512>(in, out, g, co, zchunk, st);
+    case 16 + 0: return launch_fused_cfg<T, T, 3, 4, 4, 160>(in, out, g, co, zchunk, st);
+    case 16 + 1: return launch_fused_cfg<T, T, 3, 8, 4, 288>(in, out, g, co, zchunk, st);
+    case 16 + 2: return launch_fused_cfg<T, T, 3, 4, 8, 288>(in, out, g, co, zchunk, st);
+    case 24 + 0: return launch_fused_cfg<T, T, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
+    case 24 + 1: return launch_fused_cfg<T, T, 4, 4, 2, 128>(in, out, g, co, zchunk, st);
+    case 24 + 2: return launch_fused_cfg<T, T, 4, 8, 2, 256>(in, out, g, co, zchunk, st);
   }
   return cudaErrorInvalidValue;
 }

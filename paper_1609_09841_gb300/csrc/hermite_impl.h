@@ -38,7 +38,10 @@ struct EvolveParams {
 
 // Host-side construction (exact rational arithmetic, then rounded once).
 void build_H(int m, double *H);  // P x P row-major
-void build_step_coeffs(int m, const double h[3], double c, double tau, bool adjoint,
+// mode: the half step S (kForward), its transpose S^T (kAdjoint), or its
+// derivative dS/dc with respect to the wave speed (kDc).
+enum CoeffMode { kForward = 0, kAdjoint = 1, kDc = 2 };
+void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
                        StepCoeffs<double> *out);
 void build_interp_coeffs(int m, InterpCoeffs<double> *out);
 
@@ -72,10 +75,14 @@ enum StateKind { kF64 = 0, kF32 = 1 };
 
 // Fused half step (forward or adjoint: the adjoint is the same kernel with
 // transposed tables and the mirrored offset).
-cudaError_t launch_fused_f64(int m, const double *in, double *out, const Geom &g,
+// `tile` selects one of fused_tile_count(prec, m) compiled tile shapes.
+int fused_tile_count(int prec, int m);
+cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,
                              const StepCoeffs<double> &co, int zchunk, cudaStream_t st);
-cudaError_t launch_fused_f32(int m, int state, const void *in, void *out, const Geom &g,
-                             const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+cudaError_t launch_fused_f32_s32(int m, int tile, const float *in, float *out, const Geom &g,
+                                 const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+cudaError_t launch_fused_f32_s64(int m, int tile, const double *in, double *out, const Geom &g,
+                                 const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
 
 // Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
 // output z-layers [z0, z0 + nzl); evolution reads it and writes the new node
@@ -91,5 +98,17 @@ cudaError_t launch_error(int state, const void *a, const double *b, int m, size_
                          unsigned mask, double *partial, int blocks, double *result,
                          cudaStream_t st);
 int error_blocks();
+
+// FP64 dot product sum_i a_i b_i of two states (a of the state type, b the
+// same type), same partial/result scratch convention as launch_error.
+cudaError_t launch_dot(int state, const void *a, const void *b, size_t n, double *partial, int blocks,
+                       double *result, cudaStream_t st);
+
+// Receivers: out[k] = value of u at flat node index idx[k]; adjoint: add w[k]
+// to the same entries of an adjoint state.
+cudaError_t launch_record(int state, const void *s, const long long *idx, int count, double *out,
+                          cudaStream_t st);
+cudaError_t launch_inject(int state, void *adj, const long long *idx, int count, const double *w,
+                          cudaStream_t st);
 
 }  // namespace hermite

@@ -105,9 +105,37 @@ __global__ void __launch_bounds__(kErrThreads)
     result[4] = v.nonfinite;
   }
 }
+template <typename TS>
+__global__ void __launch_bounds__(kErrThreads)
+    dot_partial_kernel(const TS *__restrict__ a, const TS *__restrict__ b, size_t n, double *__restrict__ partial) {
+  Acc v{0, 0, 0, 0, 0};
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v.sdd = fma((double)a[i], (double)b[i], v.sdd);
+  v = block_reduce(v);
+  if (threadIdx.x == 0) {
+    double *p = partial + (size_t)blockIdx.x * 8;
+    p[0] = 0;
+    p[1] = 0;
+    p[2] = v.sdd;
+    p[3] = 0;
+    p[4] = 0;
+  }
+}
 }  // namespace
 
 int error_blocks() { return kErrBlocks; }
+
+cudaError_t launch_dot(int state, const void *a, const void *b, size_t n, double *partial, int blocks,
+                       double *result, cudaStream_t st) {
+  if (state == kF64)
+    dot_partial_kernel<double><<<blocks, kErrThreads, 0, st>>>((const double *)a, (const double *)b, n, partial);
+  else
+    dot_partial_kernel<float><<<blocks, kErrThreads, 0, st>>>((const float *)a, (const float *)b, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  error_final_kernel<<<1, kErrThreads, 0, st>>>(partial, blocks, result);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_error(int state, const void *a, const double *b, int m, size_t plane,
                          unsigned mask, double *partial, int blocks, double *result,

@@ -113,8 +113,9 @@ void build_interp_coeffs(int m, InterpCoeffs<double> *out) {
 // G_a[r][col] = (r+2a)!/r! H[r+2a][col] (zero when r + 2a > 2m+1): the
 // coefficients of order r <= m of d^{2a}/dxi^{2a} applied to the interpolant
 // (Alg. 3 twice per power of the Laplacian, then truncation of Sec. 2).
-void build_step_coeffs(int m, const double h[3], double c, double tau, bool adjoint,
+void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
                        StepCoeffs<double> *out) {
+  const bool adjoint = mode == kAdjoint;
   const int M = m + 1, P = 2 * m + 2;
   Q Hq[8][8];
   exact_H(m, Hq);
@@ -158,6 +159,13 @@ void build_step_coeffs(int m, const double h[3], double c, double tau, bool adjo
     beta[0][1][s] = adjoint ? vu[s] : uv[s];
     beta[1][0][s] = adjoint ? uv[s] : vu[s];
   }
+  // Every term of grade s carries prod_k lam_k^(2 a_k), proportional to
+  // c^(2s); beta does not depend on c.  Hence dS/dc is the same sum with
+  // beta_s replaced by (2 s / c) beta_s.
+  if (mode == kDc)
+    for (int fo = 0; fo < 2; ++fo)
+      for (int fi = 0; fi < 2; ++fi)
+        for (int s = 0; s < 3; ++s) beta[fo][fi][s] *= 2.0 * s / c;
   for (int a = 0; a < 3; ++a)
     for (int q = 0; q < 16; ++q) {
       out->gx[a][q] = GR[0][a][q];

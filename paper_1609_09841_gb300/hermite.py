@@ -102,6 +102,35 @@ class Plan:
                                                  ctypes.c_void_p(_ptr(g_in)[0]), int(parity), _stream(stream)))
         return g_in
 
+    def step_dc(self, x_in, x_out, parity, stream=None):
+        """x_out = (dS_parity/dc) x_in (device tensors)."""
+        self._check(x_in, x_out)
+        capi.check(capi.lib.hermite_step_dc(self.handle, ctypes.c_void_p(_ptr(x_in)[0]),
+                                            ctypes.c_void_p(_ptr(x_out)[0]), int(parity), _stream(stream)))
+        return x_out
+
+    def dot(self, a, b, stream=None):
+        """FP64 sum of a * b over every entry of two device states."""
+        self._check(a, b)
+        out = ctypes.c_double()
+        capi.check(capi.lib.hermite_dot(self.handle, ctypes.c_void_p(_ptr(a)[0]), ctypes.c_void_p(_ptr(b)[0]),
+                                        ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def record(self, x, idx, out, stream=None):
+        """out[k] (FP64 device) = value of u at flat node idx[k] (int64 device)."""
+        self._check(x)
+        capi.check(capi.lib.hermite_record(self.handle, ctypes.c_void_p(_ptr(x)[0]), ctypes.c_void_p(idx.data_ptr()),
+                                           int(idx.numel()), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def inject(self, adj, idx, w, stream=None):
+        """adj[u value at idx[k]] += w[k] (the transpose of record)."""
+        self._check(adj)
+        capi.check(capi.lib.hermite_inject(self.handle, ctypes.c_void_p(_ptr(adj)[0]), ctypes.c_void_p(idx.data_ptr()),
+                                           int(idx.numel()), ctypes.c_void_p(w.data_ptr()), _stream(stream)))
+        return adj
+
     def error(self, x, ref, mask=0b111, stream=None):
         """(max_abs, max_rel, rms, l2_rel) of x - ref (ref FP64, device tensors)."""
         self._check(x, ref)

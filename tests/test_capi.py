@@ -105,3 +105,15 @@ def test_step_without_gpu_fails_cleanly(capi):
     rc = capi.lib.hermite_step(p, a.ctypes.data_as(ctypes.c_void_p), b.ctypes.data_as(ctypes.c_void_p), 0, None)
     assert rc < 0
     capi.lib.hermite_destroy(p)
+
+
+def test_schedule_validation(capi):
+    rc, p = _plan(capi, m=3, prec=1, state=1)
+    assert rc == 0
+    count = capi.lib.hermite_schedule_count(p)
+    assert count >= 2
+    assert capi.lib.hermite_set_schedule(p, count - 1, 8) == 0
+    assert capi.lib.hermite_set_schedule(p, count, 8) == -1
+    assert capi.lib.hermite_set_schedule(p, 0, 0) == -1
+    assert capi.lib.hermite_set_schedule(None, 0, 8) == -1
+    capi.lib.hermite_destroy(p)

@@ -132,26 +132,39 @@ def test_invalid_buffers_rejected(torch_cuda):
 def fp32_bound(m, n, h, c, dt, parity, x):
     """Elementwise tolerance of an FP32-arithmetic half step.
 
-    Each output is a sum of products; computing it in FP32 from FP32 data
-    errs by at most about k * eps32 * (|W| |x|)_i, with W the half step's
-    per-cell matrix and k the number of rounding steps along the longest
-    chain of the factorised evaluation (x-, y- and z-passes, butterflies,
-    input rounding): k <= 48 for m <= 3.  The factorised evaluation can have
-    larger intermediate sums than |W| |x| (|Gz||Gy||Gx| >= |W| entrywise), so
-    the bound uses the absolute value of each 1-D factor: it is the oracle's
-    half step with every corner block replaced by its absolute value, which
-    majorises both."""
-    M = m + 1
+    The kernel evaluates each output as a chain of 1-D contractions (x, y,
+    z) of the factors G_a = lam^(2a)/a! T1 (d^2/dxi^2)^a H (Alg. 3 twice per
+    Laplacian power, truncation of Sec. 2) weighted by the 4-term Taylor
+    coefficients beta_s of the field coupling.  Standard forward error
+    analysis of such a chain of sums of products gives
+    |err| <= gamma_k * (sum_s |beta_s| sum_{a+b+c=s} |Gz_c| x |Gy_b| x |Gx_a|) |x|
+    with gamma_k = k eps32 / (1 - k eps32) and k the number of roundings
+    along the longest chain: input conversion, three butterflies, M + 3M + 6M
+    accumulations, output conversion -> k = 10 M + 6."""
+    from math import factorial
+    M, P = m + 1, 2 * m + 2
     eps32 = 2.0 ** -24
-    s = 0 if parity == 0 else -1
-    W = oracle.cell_matrix(m, h, c, dt)
-    blocks = oracle.corner_blocks(np.abs(W), m)
-    X = np.abs(x).reshape((2 * M ** 3,) + x.shape[-3:])
-    acc = np.zeros((2 * M ** 3, X[0].size))
-    for (a, b, cc), Wb in blocks.items():
-        sh = np.roll(X, shift=(-(s + cc), -(s + b), -(s + a)), axis=(1, 2, 3))
-        acc += Wb @ sh.reshape(2 * M ** 3, -1)
-    return 48 * eps32 * acc.reshape(x.shape)
+    k = 10 * M + 6
+    gamma = k * eps32 / (1 - k * eps32)
+    tau = dt / 2
+    H = oracle.hermite_matrix(m)
+    A = np.zeros((3, 3, M, P))                      # |G_a| per dimension
+    for d in range(3):
+        lam2 = (c * tau / h[d]) ** 2
+        for a in range(3):
+            D = np.eye(P)
+            for _ in range(a):
+                D = oracle.second_derivative(D, 0)
+            A[d, a] = np.abs(lam2 ** a / factorial(a) * (D @ H)[:M])
+    beta = np.abs(np.array([[[1, .5, 1 / 12], [tau, tau / 6, 0]], [[0, 1 / tau, 1 / (3 * tau)], [1, .5, 1 / 12]]]))
+    U = np.abs(oracle.gather_cells(x, m, parity))    # (cells, 2, P, P, P) [tz, ty, tx]
+    out = np.zeros((U.shape[0], 2, M, M, M))
+    for a in range(3):
+        for b in range(3 - a):
+            for cc in range(3 - a - b):
+                T = np.einsum("za,yb,xc,nfabc->nfzyx", A[2, cc], A[1, b], A[0, a], U)
+                out += np.einsum("of,nfzyx->nozyx", beta[:, :, a + b + cc], T)
+    return gamma * out.reshape(x.shape[-3:] + (2, M, M, M)).transpose(3, 4, 5, 6, 0, 1, 2)
 
 
 @pytest.mark.parametrize("m", [1, 2, 3])
@@ -227,3 +240,28 @@ def test_standing_mode_config1_matches_oracle(torch_cuda):
         assert _relmax(out, ref) <= 1e-12
         vals, rc = plan.error(a, torch.from_numpy(closed).cuda(), 0b001)
         assert abs(vals[0] - oracle.error_norms(ref, closed, 0b001)[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("prec,state", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "fp64")])
+def test_every_schedule_matches_oracle(torch_cuda, m, prec, state):
+    """Every compiled tile shape, with z-chunks that leave a partial last
+    chunk, on a grid with ragged tiles in x and y."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import capi
+    n = (21, 11, 7)
+    plan, h, dt = _plan(m, n, prec=prec, state=state)
+    x = HI.random_state(m, n, seed=50 + m)
+    if state == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x).cuda().to(plan.torch_dtype)
+    yd = torch.empty_like(xd)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    for tile in range(capi.lib.hermite_schedule_count(plan.handle)):
+        for zc in (1, 3, 16):
+            capi.check(capi.lib.hermite_set_schedule(plan.handle, tile, zc))
+            for parity in (0, 1):
+                yd.fill_(float("nan"))
+                plan.step(xd, yd, parity)
+                ref = oracle.half_step(x, m, h, 1.0, dt, parity)
+                assert _relmax(yd.cpu().numpy().astype(np.float64), ref) <= tol, (tile, zc, parity)
