@@ -147,6 +147,39 @@ int hermite_inject(hermite_plan_t plan, void *adj_state, const long long *idx, i
 int hermite_schedule_count(hermite_plan_t plan);
 int hermite_set_schedule(hermite_plan_t plan, int tile, int zchunk);
 
+/* Batched half step: nsims independent simulations, simulation i with order
+ * m[i], grid grid[3i..3i+2], spacings h[3i..3i+2], wave speed c[i] and full
+ * time step dt[i] (each checked as hermite_plan would), all with the same
+ * precision and state type, advanced together by one persistent kernel launch
+ * per half step.  The work list of (simulation, xy-tile, z-chunk) items is
+ * handed out by an atomic counter, heaviest order first.  The returned plan
+ * works only with the hermite_batch_* calls and hermite_destroy.  Creating it
+ * allocates the per-simulation tables and the work list on the current
+ * device. */
+int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *grid, const double *h,
+                       const double *c, const double *dt, int prec, int state_dtype);
+
+/* State elements of simulation `sim` of a batched plan (0 if out of range). */
+size_t hermite_batch_elems(hermite_plan_t plan, int sim);
+
+/* z-chunk (cells per work item along x3) for orders 1, 2, 3; rebuilds the
+ * work list and drops cached descriptor sets and graphs.  Default 16. */
+int hermite_batch_set_schedule(hermite_plan_t plan, const int zchunk[3]);
+
+/* One half step of every simulation: out[i] = S_parity(in[i]).  in and out
+ * are arrays of nsims device pointers.  The first call with a given pointer
+ * set uploads a descriptor array (synchronously) and keeps it for later calls. */
+int hermite_batch_step(hermite_plan_t plan, const void *const *in, void *const *out, int parity,
+                       void *stream);
+
+/* nhalf half steps of every simulation from the primal grid, ping-ponging
+ * between the device buffer sets a[] and b[] (step k reads a if k is even, b if
+ * odd, and writes the other; parity k % 2); the result is in a if nhalf is
+ * even, else in b.  The steps are captured once into a CUDA graph (on a
+ * plan-owned stream; call it the first time outside any stream capture) and
+ * the graph is launched on `stream`. */
+int hermite_batch_run(hermite_plan_t plan, void *const *a, void *const *b, int nhalf, void *stream);
+
 /* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
 size_t hermite_state_elems(hermite_plan_t plan);
 

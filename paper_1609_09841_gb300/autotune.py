@@ -64,3 +64,31 @@ def tune(plan, x, y, zchunks=ZCHUNKS, reps=2, cache=DEFAULT_CACHE, force=False):
             json.dump(db, fh, indent=1)
         os.replace(tmp, cache)
     return best
+
+
+BATCH_ZCHUNKS = ((8, 8, 8), (16, 16, 16), (32, 16, 8), (32, 32, 16), (64, 32, 16), (96, 48, 32))
+
+
+def tune_batch(bplan, a, b, options=BATCH_ZCHUNKS, reps=2):
+    """Pick and apply the fastest per-order z-chunks of a batched plan by
+    timing `reps` batched half steps for each option; returns
+    {"zchunk", "ms", "table"}."""
+    import torch
+    table = {}
+    for zc in options:
+        bplan.set_schedule(zc)
+        bplan.step(a, b, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            if r % 2 == 0:
+                bplan.step(a, b, 0)
+            else:
+                bplan.step(b, a, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        table[zc] = e0.elapsed_time(e1) / reps
+    best = min(table, key=table.get)
+    bplan.set_schedule(best)
+    return {"zchunk": list(best), "ms": table[best], "table": {str(k): v for k, v in table.items()}}

@@ -53,6 +53,11 @@ def _load():
         "hermite_destroy": (None, [P]),
         "hermite_step_dc": (I, [P, P, P, I, P]),
         "hermite_schedule_count": (I, [P]),
+        "hermite_batch_plan": (I, [ctypes.POINTER(P), I, IP, IP, DP, DP, DP, I, I]),
+        "hermite_batch_elems": (S, [P, I]),
+        "hermite_batch_set_schedule": (I, [P, IP]),
+        "hermite_batch_step": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
+        "hermite_batch_run": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "hermite_set_schedule": (I, [P, I, I]),
         "hermite_dot": (I, [P, P, P, DP, P]),
         "hermite_record": (I, [P, P, P, I, P, P]),

@@ -13,32 +13,12 @@
 
 #include "../../include/hermite.h"
 #include "hermite_impl.h"
+#include "plan.h"
 
 using namespace hermite;
 
-struct hermite_plan_s {
-  int m;
-  int n[3];
-  double h[3];
-  double c, dt, tau;
-  int prec, state, variant;
-  size_t elems;
-  double H[64];
-  StepCoeffs<double> fwd, adj, dc;
-  StepCoeffs<float> fwd32, adj32, dc32;
-  InterpCoeffs<double> interp;
-  EvolveParams evolve;
-  int tile;                 // fused kernel: index of the compiled tile shape
-  int zchunk;               // fused kernel: cells per CTA along x3
-  size_t ws_limit;          // split variant: workspace budget in bytes
-  void *ws = nullptr;       // split workspace (device), grown on demand
-  size_t ws_bytes = 0;
-  void *stage[2] = {nullptr, nullptr};  // host-buffer steps: device copies of in / out
-  double *red = nullptr;    // error reduction scratch (device)
-  double *red_host = nullptr;  // pinned result
-};
 
-namespace {
+namespace hermite {
 
 thread_local std::string g_last_error;
 
@@ -55,6 +35,10 @@ int fail(int code, const char *fmt, ...) {
 int cuda_fail(cudaError_t e, const char *what) {
   return fail(HERMITE_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+}  // namespace hermite
+
+namespace {
 
 // Stability limit of c*tau/h per order, from the largest spectral radius of
 // the Fourier symbol of the isotropic half step over theta in [0, pi]^3
@@ -245,10 +229,10 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
 
 size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
 
-int hermite_schedule_count(hermite_plan_t p) { return p ? fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m) : 0; }
+int hermite_schedule_count(hermite_plan_t p) { return p && !p->batch ? fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m) : 0; }
 
 int hermite_set_schedule(hermite_plan_t p, int tile, int zchunk) {
-  if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
   if (tile < 0 || tile >= hermite_schedule_count(p)) return fail(HERMITE_EINVAL, "tile %d out of range", tile);
   if (zchunk < 1 || zchunk > 4096) return fail(HERMITE_EINVAL, "zchunk %d out of range", zchunk);
   p->tile = tile;
@@ -265,6 +249,7 @@ int hermite_plan_operator(hermite_plan_t p, double *out) {
 
 int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
   if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
   cudaStream_t st = (cudaStream_t)stream;
@@ -301,6 +286,7 @@ int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *
 
 int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, int parity, void *stream) {
   if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   int rc = check_device_pair(p, out_adj, in_adj);
   if (rc) return rc;
@@ -311,6 +297,7 @@ int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, in
 
 int hermite_step_dc(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
   if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   int rc = check_device_pair(p, in, out);
   if (rc) return rc;
@@ -341,6 +328,7 @@ int hermite_inject(hermite_plan_t p, void *adj, const long long *idx, int count,
 int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned mask, double out[4],
                   void *stream) {
   if (!p || !state || !ref || !out) return fail(HERMITE_EINVAL, "null argument");
+  if (p->batch) return fail(HERMITE_EINVAL, "batched plan");
   if ((mask & 3u) == 0) return fail(HERMITE_EINVAL, "component mask selects no field");
   if (classify(state) != kDevicePtr || classify(ref) != kDevicePtr)
     return fail(HERMITE_EINVAL, "hermite_error takes device buffers");
@@ -369,6 +357,7 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
 
 int hermite_dot(hermite_plan_t p, const void *a, const void *b, double *out, void *stream) {
   if (!p || !a || !b || !out) return fail(HERMITE_EINVAL, "null argument");
+  if (p->batch) return fail(HERMITE_EINVAL, "batched plan");
   if (classify(a) != kDevicePtr || classify(b) != kDevicePtr) return fail(HERMITE_EINVAL, "hermite_dot takes device buffers");
   int rc = ensure_red(p);
   if (rc) return rc;
@@ -386,6 +375,7 @@ int hermite_dot(hermite_plan_t p, const void *a, const void *b, double *out, voi
 
 void hermite_destroy(hermite_plan_t p) {
   if (!p) return;
+  if (p->batch) destroy_batch(p->batch);
   if (p->ws) cudaFree(p->ws);
   for (int k = 0; k < 2; ++k)
     if (p->stage[k]) cudaFree(p->stage[k]);

@@ -1,0 +1,144 @@
+// Batched half step: many independent simulations (each its own order m,
+// grid and time step) advanced by ONE persistent launch.  The host builds a
+// work list of (simulation, xy-tile, z-chunk) items, heaviest order first;
+// each resident CTA takes the next item with an atomic counter, copies that
+// simulation's tables into shared memory and runs the fused tile body of its
+// order (the same code as the single-grid kernel).  No CTA ever waits on
+// another, so there is nothing to time out.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "fused.cuh"
+
+namespace hermite {
+
+// Tile shapes of the batched kernel per order (NT = 256 threads for all).
+template <int M> struct BatchTile;
+template <> struct BatchTile<2> { static constexpr int TX = 8, TY = 8; };
+template <> struct BatchTile<3> { static constexpr int TX = 8, TY = 4; };
+template <> struct BatchTile<4> { static constexpr int TX = 4, TY = 4; };
+constexpr int kBatchThreads = 256;
+
+void batch_tile_shape(int m, int *tx, int *ty) {
+  switch (m) {
+    case 1: *tx = BatchTile<2>::TX; *ty = BatchTile<2>::TY; break;
+    case 2: *tx = BatchTile<3>::TX; *ty = BatchTile<3>::TY; break;
+    default: *tx = BatchTile<4>::TX; *ty = BatchTile<4>::TY; break;
+  }
+}
+
+template <typename TC>
+constexpr size_t batch_smem_bytes() {
+  constexpr size_t a = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>::SMEM;
+  constexpr size_t b = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>::SMEM;
+  constexpr size_t c = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>::SMEM;
+  constexpr size_t mx = a > b ? (a > c ? a : c) : (b > c ? b : c);
+  return mx + sizeof(StepCoeffs<TC>);
+}
+
+template <typename TS, typename TC, int M>
+__device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
+                                           TC *sX, TC *sY, int s) {
+  constexpr int TX = BatchTile<M>::TX, TY = BatchTile<M>::TY;
+  Geom g;
+  g.nx = sm.n[0];
+  g.ny = sm.n[1];
+  g.nz = sm.n[2];
+  g.s = s;
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
+  const int z0 = it.z0, z1 = min(it.z0 + sm.zchunk, g.nz);
+  fused_tile<TS, TC, M, TX, TY, kBatchThreads>((const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sY);
+}
+
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kBatchThreads)
+    batch_step_kernel(const BatchSim *__restrict__ sims, const StepCoeffs<TC> *__restrict__ coeffs,
+                      const BatchItem *__restrict__ items, int nitems, int *__restrict__ counter, int s) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StepCoeffs<TC> *sco = reinterpret_cast<StepCoeffs<TC> *>(smem_raw);
+  TC *sX = reinterpret_cast<TC *>(smem_raw + ((sizeof(StepCoeffs<TC>) + 15) / 16) * 16);
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();  // also orders the previous tile's last reads before the copy below
+    const int i = s_item;
+    if (i >= nitems) break;
+    const BatchItem it = items[i];
+    const BatchSim sm = sims[it.sim];
+    {
+      const TC *src = reinterpret_cast<const TC *>(coeffs + it.sim);
+      TC *dst = reinterpret_cast<TC *>(sco);
+      for (int k = threadIdx.x; k < (int)(sizeof(StepCoeffs<TC>) / sizeof(TC)); k += kBatchThreads) dst[k] = src[k];
+    }
+    __syncthreads();
+    switch (sm.m) {
+      case 1: {
+        using Sh = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>;
+        batch_tile<TS, TC, 2>(sm, it, *sco, sX, sX + Sh::SX, s);
+        break;
+      }
+      case 2: {
+        using Sh = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>;
+        batch_tile<TS, TC, 3>(sm, it, *sco, sX, sX + Sh::SX, s);
+        break;
+      }
+      default: {
+        using Sh = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>;
+        batch_tile<TS, TC, 4>(sm, it, *sco, sX, sX + Sh::SX, s);
+        break;
+      }
+    }
+    __syncthreads();  // every thread is done with sco, sX, sY and s_item
+  }
+}
+
+template <typename TS, typename TC>
+static bool &batch_attr_done() {  // dynamic shared memory attribute set for this instantiation
+  static bool done = false;
+  return done;
+}
+
+template <typename TS, typename TC>
+static cudaError_t launch_batch_t(const BatchSim *sims, const void *coeffs, const BatchItem *items, int nitems,
+                                  int *counter, int s, int grid, cudaStream_t st) {
+  auto kern = batch_step_kernel<TS, TC>;
+  constexpr size_t smem = batch_smem_bytes<TC>() + 16;
+  if (!batch_attr_done<TS, TC>()) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_attr_done<TS, TC>() = true;
+  }
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kBatchThreads, smem, st>>>(sims, (const StepCoeffs<TC> *)coeffs, items, nitems, counter, s);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TC>
+static int occupancy_t() {
+  int blocks = 0;
+  constexpr size_t smem = batch_smem_bytes<TC>() + 16;
+  auto kern = batch_step_kernel<TS, TC>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+    batch_attr_done<TS, TC>() = true;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kBatchThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return blocks > 0 ? blocks : 1;
+}
+
+int batch_blocks_per_sm(int compute, int state) {
+  if (compute == kF64) return occupancy_t<double, double>();
+  return state == kF64 ? occupancy_t<double, float>() : occupancy_t<float, float>();
+}
+
+cudaError_t launch_batch(int compute, int state, const BatchSim *sims, const void *coeffs, const BatchItem *items,
+                         int nitems, int *counter, int s, int grid, cudaStream_t st) {
+  if (compute == kF64) return launch_batch_t<double, double>(sims, coeffs, items, nitems, counter, s, grid, st);
+  if (state == kF64) return launch_batch_t<double, float>(sims, coeffs, items, nitems, counter, s, grid, st);
+  return launch_batch_t<float, float>(sims, coeffs, items, nitems, counter, s, grid, st);
+}
+
+}  // namespace hermite

@@ -1,0 +1,31 @@
+// Device-side descriptors of the batched half step.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hermite_impl.h"
+
+namespace hermite {
+
+struct BatchSim {      // one simulation of a batch, as the kernel sees it
+  const void *in;      // input state (plan's state type)
+  void *out;           // output state
+  int n[3];            // nodes along x1, x2, x3
+  int m;               // order
+  int zchunk;          // cells per work item along x3
+  int pad;
+};
+
+struct BatchItem {     // one unit of work: a TX x TY x zchunk block of one simulation
+  int sim;
+  int tile;            // xy-tile index (x fastest)
+  int z0;              // first output z layer
+  int pad;
+};
+
+void batch_tile_shape(int m, int *tx, int *ty);
+int batch_blocks_per_sm(int compute, int state);
+cudaError_t launch_batch(int compute, int state, const BatchSim *sims, const void *coeffs, const BatchItem *items,
+                         int nitems, int *counter, int s, int grid, cudaStream_t st);
+
+}  // namespace hermite

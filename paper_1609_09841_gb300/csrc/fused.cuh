@@ -46,10 +46,15 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
+// One tile: output nodes [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of one grid.
+// sX, sY: shared memory of FusedShape<TC, M, TX, TY>::SX and ::SY elements.
+// All NT threads of the CTA must call it; it starts and ends without a
+// pending barrier (callers that reuse sX, sY or `co` for another tile must
+// put a __syncthreads() between the calls).
 template <typename TS, typename TC, int M, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
-    fused_step_kernel(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
-                      const StepCoeffs<TC> co) {
+__device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
+                                           int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
+                                           TC *__restrict__ sX, TC *__restrict__ sY) {
   using Sh = FusedShape<TC, M, TX, TY>;
   constexpr int NYN = Sh::NYN, NA = Sh::NA;
   constexpr int XPT = (Sh::XITEMS + NT - 1) / NT;
@@ -57,17 +62,7 @@ __global__ void __launch_bounds__(NT)
   constexpr int ZPT = (Sh::ZITEMS + NT - 1) / NT;
   constexpr int XS = NYN * TX;  // stride of one (f, iz, iy, a, ix') row of sX
   constexpr int YS = TY * TX;   // stride of one (f, g, iz, iy', ix') row of sY
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC *sX = reinterpret_cast<TC *>(smem_raw);
-  TC *sY = sX + Sh::SX;
-
   const int nx = g.nx, ny = g.ny, nz = g.nz, s = g.s;
-  const int tiles_x = (nx + TX - 1) / TX;
-  const int x0 = (blockIdx.x % tiles_x) * TX;
-  const int y0 = (blockIdx.x / tiles_x) * TY;
-  const int z0 = blockIdx.y * zchunk;
-  if (z0 >= nz) return;
-  const int z1 = min(z0 + zchunk, nz);
   const size_t pxy = (size_t)nx * ny;
   const size_t plane = pxy * nz;
 
@@ -229,6 +224,22 @@ __global__ void __launch_bounds__(NT)
           for (int iz = 0; iz < M; ++iz) prev[k][f][gg][iz] = cur[f][gg][iz];
     }
   }
+}
+
+template <typename TS, typename TC, int M, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+    fused_step_kernel(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
+                      const StepCoeffs<TC> co) {
+  using Sh = FusedShape<TC, M, TX, TY>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC *sX = reinterpret_cast<TC *>(smem_raw);
+  TC *sY = sX + Sh::SX;
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % tiles_x) * TX;
+  const int y0 = (blockIdx.x / tiles_x) * TY;
+  const int z0 = blockIdx.y * zchunk;
+  if (z0 >= g.nz) return;
+  fused_tile<TS, TC, M, TX, TY, NT>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.nz), co, sX, sY);
 }
 
 template <typename TS, typename TC, int M, int TX, int TY, int NT>

@@ -117,3 +117,17 @@ def test_schedule_validation(capi):
     assert capi.lib.hermite_set_schedule(p, 0, 0) == -1
     assert capi.lib.hermite_set_schedule(None, 0, 8) == -1
     capi.lib.hermite_destroy(p)
+
+
+def test_batched_plan_rejected_by_single_calls_without_gpu(capi):
+    """Argument checks of the batched plan that need no device."""
+    p = ctypes.c_void_p()
+    one = (ctypes.c_int * 1)(1)
+    g = (ctypes.c_int * 3)(8, 8, 8)
+    h = (ctypes.c_double * 3)(0.125, 0.125, 0.125)
+    c = (ctypes.c_double * 1)(1.0)
+    dt_bad = (ctypes.c_double * 1)(1.0)
+    assert capi.lib.hermite_batch_plan(ctypes.byref(p), 0, one, g, h, c, dt_bad, 1, 1) == -1
+    assert capi.lib.hermite_batch_plan(ctypes.byref(p), 1, one, g, h, c, dt_bad, 1, 1) == -5
+    assert capi.lib.hermite_batch_plan(ctypes.byref(p), 1, one, g, h, c, dt_bad, 0, 1) == -4
+    assert not p.value
