@@ -180,6 +180,36 @@ int hermite_batch_step(hermite_plan_t plan, const void *const *in, void *const *
  * the graph is launched on `stream`. */
 int hermite_batch_run(hermite_plan_t plan, void *const *a, void *const *b, int nhalf, void *stream);
 
+/* Allocation-free half step (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory).  Callers that run while
+ * another library owns the device memory (a framework's caching allocator or
+ * a fixed memory budget), or time-critical loops that must not pay for
+ * cudaMalloc or risk fragmentation, can call this instead of hermite_step.
+ * It computes exactly what hermite_step computes with the SPLIT variant
+ * (same kernels, same results) for device buffers in and out, which the
+ * caller still provides, but its workspace is a static device array of
+ * HERMITE_STATIC_WORKSPACE_BYTES (16 MiB) that every GPU loading the library
+ * holds until the process exits, and it calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ *   - Size limit: one z-layer of cell polynomials, 2 (2m+2)^3 n1 n2 values of
+ *     the arithmetic type, must fit in the array; otherwise EINVAL with a
+ *     message naming both sizes.  Larger grids are processed in z-slabs.
+ *   - Set-up: the first call on each device looks up the array's device
+ *     address (cudaGetSymbolAddress) with that device current; make that
+ *     first call outside any stream capture.
+ *   - Sharing: every call on a device uses the same array and leaves its last
+ *     contents there (nothing in it needs to start at zero: each call writes
+ *     every entry it reads).  Calls whose work overlaps on the GPU (different
+ *     streams, or graphs replayed concurrently) race on the array; order them
+ *     on one stream.
+ * Same argument rules and error codes as hermite_step (device pointers). */
+#define HERMITE_STATIC_WORKSPACE_BYTES ((size_t)16 << 20)
+int hermite_step_split_static(hermite_plan_t plan, const void *in_state, void *out_state, int parity,
+                              void *stream);
+
+/* HERMITE_STATIC_WORKSPACE_BYTES, as compiled into the library. */
+size_t hermite_static_workspace_bytes(void);
+
 /* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
 size_t hermite_state_elems(hermite_plan_t plan);
 
