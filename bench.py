@@ -30,6 +30,18 @@ N_SIDE = 256
 METRIC = "Hermite DOF-updates/s per half step (m=3, 256^3), FP64 vs mixed at stated error"
 
 
+# Algorithmic flop per output node of the fused half step (FMA = 2 flop, butterfly add = 1):
+# x-pass 6M^4 FMA + 4M^3 adds per edge, y-pass 12M^4 + 12M^3 per face, z-pass 12M^4 + 12M^3
+# per cell, both fields, M = m + 1.
+FLOP_PER_NODE = {m: 2 * 30 * (m + 1) ** 4 + 28 * (m + 1) ** 3 for m in (1, 2, 3)}
+# FP32 SIMT peak of a GB300 at its maximum SM clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 kernel (ncu capture at
+# 128^3 scaled by the node count: 2.218 GB x 8), for the bench's schedule.
+TRAFFIC_BYTES = {(3, 256): 17.74e9}
+FP64_PEAK_TFLOPS = 1.25
+
+
 def dof_per_step(m=M_ORDER, n=N_SIDE):
     return 2 * (m + 1) ** 3 * n ** 3
 
@@ -45,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (profiling runs use a smaller one)")
     ap.add_argument("--m", type=int, default=M_ORDER)
+    ap.add_argument("--tile", type=int, default=-1, help="fixed schedule of the mixed leg (skips autotuning)")
+    ap.add_argument("--zchunk", type=int, default=16)
     ap.add_argument("--legs", default="mixed,mixed64,fp64,e2e",
                     help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), fp64, e2e")
     return ap.parse_args()
@@ -168,7 +182,11 @@ def run_ours(args, rank, world):
     plan = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp32")
     x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
     y = torch.empty_like(x)
-    sched = {"mixed": tune(plan, x, y, cache=None)}
+    if args.tile >= 0:
+        plan.set_schedule(args.tile, args.zchunk)
+        sched = {"mixed": {"tile": args.tile, "zchunk": args.zchunk, "ms": None}}
+    else:
+        sched = {"mixed": tune(plan, x, y, cache=None)}
     x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
     for k in range(args.warmup):
         plan.step(x, y, k % 2)
@@ -186,6 +204,7 @@ def run_ours(args, rank, world):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = traffic_alg / (ms * 1e-3) / 1e9
+    flop_node = FLOP_PER_NODE[m]
     ms_mixed64 = ms64 = e2e_s = float("nan")
     if legs & {"mixed64", "fp64"}:
         xd = x.double()
@@ -219,11 +238,26 @@ def run_ours(args, rank, world):
                                "step, FP32 arithmetic and FP32 state; inputs 8.6 GB > L2 (no flush)",
                    "global_batch": world, "parallelism": "replicas" if world > 1 else "single",
                    "variant": "fused", "dof_per_step": dof},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json)",
-                     "kernel": "fused_step_kernel<float,float,4,...>"},
+        "roofline": {"bound": "alu", "achieved": flop_node * dof / (2 * (m + 1) ** 3) / (ms * 1e-3) / 1e12,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flop_node * dof / (2 * (m + 1) ** 3) / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "traffic": TRAFFIC_BYTES.get((m, args.side)),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                     "flop_per_node": flop_node, "hbm_achieved_gbs": achieved, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": achieved / hbm_peak, "hbm_peak_source": "measured (MEASURED_PEAKS.json)",
+                     "kernel": f"fused_step_kernel<float, float, {m + 1}, ...> (schedule {sched['mixed']['tile']})"},
         "fp64": {"value": world * dof / (max_over_ranks(ms64) * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps,
-                 "dtype": "f64", "state": "fp64"},
+                 "dtype": "f64", "state": "fp64",
+                 "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
+                              "achieved": flop_node * dof / (2 * (m + 1) ** 3) / (ms64 * 1e-3) / 1e12,
+                              "frac": flop_node * dof / (2 * (m + 1) ** 3) / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (a DFMA probe measured 1.20)"},
+                 "error_vs_oracle": "1e-12 relative max-norm per half step (tests/test_gpu_parity.py)"},
+        "mixed_error_at_t1": {"workload": "m=2 Gaussian sigma=0.05 to t=1, vs the FP64 GPU path "
+                                          "(tests/test_gpu_precision.py)",
+                              "256^3": {"max_rel_all": 8.2e-4, "u_values_max_rel": 2.0e-5, "v_values_max_rel": 4.5e-5},
+                              "64^3": {"max_rel_all": 1.4e-4, "u_values_max_rel": 7.5e-6, "v_values_max_rel": 1.0e-5},
+                              "per_half_step": "within 46 eps32 x |S| |x| (tests/test_gpu_parity.py)"},
         "mixed_fp64_state": {"value": world * dof / (max_over_ranks(ms_mixed64) * 1e-3), "ms_per_step": ms_mixed64,
                              "hbm_frac": plan.elems * 8 * 2 / (ms_mixed64 * 1e-3) / 1e9 / hbm_peak},
         "speedup_mixed_vs_fp64": ms64 / ms,

@@ -16,11 +16,12 @@
 // A CTA owns TX x TY output nodes of the xy-plane and marches along x3 over
 // `zchunk` cells (Sec. 3.1's marching along x3): per node plane the x-pass
 // reads the node pairs straight from global memory (coalesced along x1, the
-// right neighbour of one thread is the left of the next, an L1 hit), writes
-// its results to shared memory; the y-pass turns them into face results; the
-// z-pass combines them with the previous plane's face results, which each
-// thread keeps in registers.  Two barriers per plane.  Every per-item index
-// is computed once before the march.
+// right neighbour of one thread is the left of the next, an L1 hit; each
+// thread issues all its loads of the plane before any arithmetic), writes
+// its results to shared memory; the y-pass turns them into face results,
+// kept for two planes (double buffer); the z-pass combines the face results
+// of planes p-1 and p.  Two barriers per plane.  Every per-item index is
+// computed once before the march.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,7 +36,7 @@ struct FusedShape {
   static constexpr int NA = (M == 2) ? 2 : 3;               // non-zero grades of G (G_2 = 0 for m = 1)
   static constexpr int SX = 2 * M * M * NA * M * NYN * TX;  // x-pass results [f][iz][iy][a][ix'][ey][ex]
   static constexpr int SY = 2 * 3 * M * M * M * TX * TY;    // y-pass results [f][g][iz][iy'][ix'][fy][fx]
-  static constexpr size_t SMEM = (size_t)(SX + SY) * sizeof(TC);
+  static constexpr size_t SMEM = (size_t)(SX + 2 * SY) * sizeof(TC);  // sY double-buffered by plane
   static constexpr int XITEMS = 2 * M * M * NYN * TX;       // (f, iz, iy, edge)
   static constexpr int YITEMS = 2 * M * M * TY * TX;        // (f, iz, ix', face)
   static constexpr int ZITEMS = M * M * TX * TY;            // (iy', ix', cell)
@@ -47,7 +48,7 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 }
 
 // One tile: output nodes [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of one grid.
-// sX, sY: shared memory of FusedShape<TC, M, TX, TY>::SX and ::SY elements.
+// sX, sY: shared memory of FusedShape<TC, M, TX, TY>::SX and 2 * ::SY elements.
 // All NT threads of the CTA must call it; it starts and ends without a
 // pending barrier (callers that reuse sX, sY or `co` for another tile must
 // put a __syncthreads() between the calls).
@@ -114,20 +115,27 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     zxy[k] = (e < Sh::ZITEMS && ox < nx && oy < ny) ? oy * nx + ox : -1;
   }
 
-  TC prev[ZPT][2][3][M];  // face results of the previous node plane, per z-item
-
   for (int p = 0; p <= z1 - z0; ++p) {
     const size_t zoff = (size_t)wrap_index(z0 + s + p, nz) * pxy;
     // x-pass on the TX x (TY+1) x-edges of node plane z0 + s + p
+    TC Lv[XPT][M], Rv[XPT][M];
 #pragma unroll
     for (int k = 0; k < XPT; ++k) {
       if (xdst[k] < 0) continue;
       const TS *src = xsrc[k] + zoff;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        Lv[k][i] = (TC)__ldg(src + i * plane + xl[k]);
+        Rv[k][i] = (TC)__ldg(src + i * plane + xr[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < XPT; ++k) {
+      if (xdst[k] < 0) continue;
       TC sv[M], dv[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        const TC L = (TC)__ldg(src + i * plane + xl[k]);
-        const TC R = (TC)__ldg(src + i * plane + xr[k]);
+        const TC L = Lv[k][i], R = Rv[k][i];
         sv[i] = (i & 1) ? R - L : R + L;
         dv[i] = (i & 1) ? R + L : R - L;
       }
@@ -157,7 +165,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
           sv[a][iy] = (iy & 1) ? R - L : R + L;
           dv[a][iy] = (iy & 1) ? R + L : R - L;
         }
-      TC *yo = sY + ydst[k];
+      TC *yo = sY + (p & 1) * Sh::SY + ydst[k];
 #pragma unroll
       for (int gg = 0; gg < 3; ++gg)
 #pragma unroll
@@ -174,21 +182,15 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         }
     }
     __syncthreads();
-    // z-pass: cell layer z0 + p - 1 from the faces of planes p - 1 and p.
-    // (The next plane's x-pass writes sX, last read by this plane's y-pass
-    // before the barrier above; its y-pass writes sY only after the next
-    // barrier, when every thread has finished this z-pass.)
+    // z-pass: cell layer z0 + p - 1 from the faces of planes p - 1 and p
+    // (the two halves of sY).  The next plane's x-pass writes sX, last read
+    // by this plane's y-pass before the barrier above; its y-pass overwrites
+    // the half of sY read here only after the next barrier.
+    if (p > 0) {
+      const TC *yc = sY + (p & 1) * Sh::SY, *yp = sY + ((p - 1) & 1) * Sh::SY;
 #pragma unroll
-    for (int k = 0; k < ZPT; ++k) {
-      if (threadIdx.x + k * NT >= Sh::ZITEMS) continue;
-      TC cur[2][3][M];
-#pragma unroll
-      for (int f = 0; f < 2; ++f)
-#pragma unroll
-        for (int gg = 0; gg < 3; ++gg)
-#pragma unroll
-          for (int iz = 0; iz < M; ++iz) cur[f][gg][iz] = sY[zsrc[k] + ((f * 3 + gg) * M + iz) * M * M * YS];
-      if (p > 0 && zxy[k] >= 0) {
+      for (int k = 0; k < ZPT; ++k) {
+        if (zxy[k] < 0) continue;
         TC sv[2][3][M], dv[2][3][M];
 #pragma unroll
         for (int f = 0; f < 2; ++f)
@@ -196,7 +198,8 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
           for (int gg = 0; gg < 3; ++gg)
 #pragma unroll
             for (int iz = 0; iz < M; ++iz) {
-              const TC L = prev[k][f][gg][iz], R = cur[f][gg][iz];
+              const int q = zsrc[k] + ((f * 3 + gg) * M + iz) * M * M * YS;
+              const TC L = yp[q], R = yc[q];
               sv[f][gg][iz] = (iz & 1) ? R - L : R + L;
               dv[f][gg][iz] = (iz & 1) ? R + L : R - L;
             }
@@ -216,12 +219,6 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
             o[(size_t)((fo * M + r) * M * M) * plane] = (TS)acc;
           }
       }
-#pragma unroll
-      for (int f = 0; f < 2; ++f)
-#pragma unroll
-        for (int gg = 0; gg < 3; ++gg)
-#pragma unroll
-          for (int iz = 0; iz < M; ++iz) prev[k][f][gg][iz] = cur[f][gg][iz];
     }
   }
 }

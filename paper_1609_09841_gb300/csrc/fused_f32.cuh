@@ -20,7 +20,7 @@ cudaError_t dispatch_f32(int m, int tile, const TS *in, TS *out, const Geom &g, 
     case 24 + 0: return launch_fused_cfg<TS, float, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
     case 24 + 1: return launch_fused_cfg<TS, float, 4, 8, 4, 256>(in, out, g, co, zchunk, st);
     case 24 + 2: return launch_fused_cfg<TS, float, 4, 8, 4, 512>(in, out, g, co, zchunk, st);
-    case 24 + 3: return launch_fused_cfg<TS, float, 4, 4, 2, 128>(in, out, g, co, zchunk, st);
+    case 24 + 3: return launch_fused_cfg<TS, float, 4, 4, 4, 128>(in, out, g, co, zchunk, st);
   }
   return cudaErrorInvalidValue;
 }

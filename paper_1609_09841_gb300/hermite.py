@@ -75,6 +75,12 @@ class Plan:
         import torch
         return torch.empty(self.shape, dtype=self.torch_dtype, device=device)
 
+    def schedule_count(self):
+        return capi.lib.hermite_schedule_count(self.handle)
+
+    def set_schedule(self, tile, zchunk):
+        capi.check(capi.lib.hermite_set_schedule(self.handle, int(tile), int(zchunk)))
+
     def operator(self):
         P = 2 * self.m + 2
         out = (ctypes.c_double * (P * P))()
