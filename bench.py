@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--m", type=int, default=M_ORDER)
     ap.add_argument("--tile", type=int, default=-1, help="fixed schedule of the mixed leg (skips autotuning)")
     ap.add_argument("--zchunk", type=int, default=16)
-    ap.add_argument("--legs", default="mixed,mixed64,fp64,e2e",
-                    help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), fp64, e2e")
+    ap.add_argument("--legs", default="mixed,mixed64,hybriddf,hybrid64,fp64,e2e",
+                    help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), hybriddf, hybrid64, fp64, e2e")
     return ap.parse_args()
 
 
@@ -206,7 +206,8 @@ def run_ours(args, rank, world):
     achieved = traffic_alg / (ms * 1e-3) / 1e9
     flop_node = FLOP_PER_NODE[m]
     ms_mixed64 = ms64 = e2e_s = float("nan")
-    if legs & {"mixed64", "fp64"}:
+    ms_hyb = {}
+    if legs & {"mixed64", "fp64", "hybriddf", "hybrid64"}:
         xd = x.double()
         yd = torch.empty_like(xd)
         if "mixed64" in legs:   # same arithmetic, FP64 state (loaded, computed in FP32, stored)
@@ -214,6 +215,12 @@ def run_ours(args, rank, world):
             sched["mixed64"] = tune(plan64s, xd, yd, cache=None)
             xd.copy_(x)
             ms_mixed64 = timed_steps(torch, plan64s, xd, yd, args.steps, args.warmup)
+        for hk in ("hybriddf", "hybrid64"):   # FP64 state, grade-0 contractions in double-float / FP64
+            if hk in legs:
+                planh = Plan(m, n, h, 1.0, dt, prec=hk, state="fp64")
+                sched[hk] = tune(planh, xd, yd, zchunks=(16, 32, 64), reps=1, cache=None)
+                xd.copy_(x)
+                ms_hyb[hk] = timed_steps(torch, planh, xd, yd, max(3, args.steps // 4), min(args.warmup, 3))
         if "fp64" in legs:      # plain FP64
             plan64 = Plan(m, n, h, 1.0, dt, prec="fp64", state="fp64")
             sched["fp64"] = tune(plan64, xd, yd, zchunks=(16, 32), reps=1, cache=None)
@@ -258,6 +265,10 @@ def run_ours(args, rank, world):
                               "256^3": {"max_rel_all": 8.2e-4, "u_values_max_rel": 2.0e-5, "v_values_max_rel": 4.5e-5},
                               "64^3": {"max_rel_all": 1.4e-4, "u_values_max_rel": 7.5e-6, "v_values_max_rel": 1.0e-5},
                               "per_half_step": "within 46 eps32 x |S| |x| (tests/test_gpu_parity.py)"},
+        "hybrid": {k: {"value": world * dof / (max_over_ranks(v) * 1e-3), "ms_per_step": v,
+                       "speedup_vs_fp64": ms64 / v,
+                       "error_at_t1": "see tests/test_gpu_precision.py (bar 1e-5, all components, vs FP64)"}
+                   for k, v in ms_hyb.items()},
         "mixed_fp64_state": {"value": world * dof / (max_over_ranks(ms_mixed64) * 1e-3), "ms_per_step": ms_mixed64,
                              "hbm_frac": plan.elems * 8 * 2 / (ms_mixed64 * 1e-3) / 1e9 / hbm_peak},
         "speedup_mixed_vs_fp64": ms64 / ms,

@@ -69,8 +69,12 @@ enum hermite_status {
 
 /* Arithmetic of the contractions (interpolation and evolution). */
 enum hermite_prec {
-  HERMITE_FP64 = 0, /* FP64 throughout (state must be FP64) */
-  HERMITE_FP32 = 1  /* FP32 contractions, state FP32 or FP64 (loaded, computed in FP32, stored) */
+  HERMITE_FP64 = 0,     /* FP64 throughout (state must be FP64) */
+  HERMITE_FP32 = 1,     /* FP32 contractions, state FP32 or FP64 (loaded, computed in FP32, stored) */
+  HERMITE_HYBRID64 = 2, /* FP64 state; every contraction applied to grade-0 data (the node data,
+                           the x- and y-interpolants) in FP64, the rest (small grade >= 1 terms of
+                           the Taylor series) in FP32.  Fused variant only. */
+  HERMITE_HYBRIDDF = 3  /* as HYBRID64 with the FP64 part in double-float (pairs of FP32) */
 };
 
 enum hermite_state_type { HERMITE_STATE_FP64 = 0, HERMITE_STATE_FP32 = 1 };

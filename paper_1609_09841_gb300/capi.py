@@ -20,6 +20,8 @@ HERMITE_ENONFINITE = -7
 
 HERMITE_FP64 = 0
 HERMITE_FP32 = 1
+HERMITE_HYBRID64 = 2
+HERMITE_HYBRIDDF = 3
 HERMITE_STATE_FP64 = 0
 HERMITE_STATE_FP32 = 1
 HERMITE_AUTO = 0

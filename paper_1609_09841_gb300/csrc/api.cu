@@ -130,6 +130,13 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
   const bool split = p->variant == HERMITE_SPLIT && mode == kForward;
   cudaError_t e = cudaSuccess;
   if (!split) {
+    if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) {
+      const HybridCoeffs &ch = mode == kAdjoint ? p->hyb_adj : (mode == kDc ? p->hyb_dc : p->hyb_fwd);
+      e = launch_hybrid(p->prec == HERMITE_HYBRID64 ? 0 : 1, p->m, p->tile, (const double *)in, (double *)out, g, ch,
+                        p->zchunk, st);
+      if (e != cudaSuccess) return cuda_fail(e, "hybrid half-step launch");
+      return HERMITE_OK;
+    }
     const StepCoeffs<double> &cd = mode == kAdjoint ? p->adj : (mode == kDc ? p->dc : p->fwd);
     const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
     if (p->prec == HERMITE_FP64)
@@ -181,13 +188,16 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   }
   if (!(c > 0.0) || !std::isfinite(c)) return fail(HERMITE_EINVAL, "wave speed c must be positive");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
-  if (prec != HERMITE_FP64 && prec != HERMITE_FP32) return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
+  if (prec != HERMITE_FP64 && prec != HERMITE_FP32 && prec != HERMITE_HYBRID64 && prec != HERMITE_HYBRIDDF)
+    return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
   if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
     return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
-  if (prec == HERMITE_FP64 && state_dtype != HERMITE_STATE_FP64)
-    return fail(HERMITE_EUNSUPPORTED, "FP64 arithmetic needs an FP64 state");
+  if (prec != HERMITE_FP32 && state_dtype != HERMITE_STATE_FP64)
+    return fail(HERMITE_EUNSUPPORTED, "FP64 and hybrid arithmetic need an FP64 state");
   if (variant != HERMITE_AUTO && variant != HERMITE_FUSED && variant != HERMITE_SPLIT)
     return fail(HERMITE_EINVAL, "variant %d unknown", variant);
+  if (variant == HERMITE_SPLIT && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
+    return fail(HERMITE_EUNSUPPORTED, "the split variant has no hybrid precision");
   const double tau = 0.5 * dt;
   for (int k = 0; k < 3; ++k) {
     const double lam = c * tau / h[k];
@@ -217,6 +227,17 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   p->fwd32 = cast_coeffs<float>(p->fwd);
   p->adj32 = cast_coeffs<float>(p->adj);
   p->dc32 = cast_coeffs<float>(p->dc);
+  const StepCoeffs<double> *srcs[3] = {&p->fwd, &p->adj, &p->dc};
+  HybridCoeffs *dsts[3] = {&p->hyb_fwd, &p->hyb_adj, &p->hyb_dc};
+  for (int k = 0; k < 3; ++k) {
+    dsts[k]->d = *srcs[k];
+    dsts[k]->hi = cast_coeffs<float>(*srcs[k]);
+    StepCoeffs<double> rest = *srcs[k];
+    double *r = &rest.gx[0][0];
+    const float *h = &dsts[k]->hi.gx[0][0];
+    for (size_t q = 0; q < sizeof(StepCoeffs<double>) / sizeof(double); ++q) r[q] -= (double)h[q];
+    dsts[k]->lo = cast_coeffs<float>(rest);
+  }
   build_interp_coeffs(m, &p->interp);
   p->evolve.tau = tau;
   for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
@@ -229,7 +250,11 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
 
 size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
 
-int hermite_schedule_count(hermite_plan_t p) { return p && !p->batch ? fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m) : 0; }
+int hermite_schedule_count(hermite_plan_t p) {
+  if (!p || p->batch) return 0;
+  if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
+  return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
+}
 
 int hermite_set_schedule(hermite_plan_t p, int tile, int zchunk) {
   if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");

@@ -153,7 +153,8 @@ int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *
   *out = nullptr;
   if (nsims < 1 || nsims > (1 << 16)) return fail(HERMITE_EINVAL, "nsims = %d out of range", nsims);
   if (!m || !grid || !h || !c || !dt) return fail(HERMITE_EINVAL, "null array argument");
-  if (prec != HERMITE_FP64 && prec != HERMITE_FP32) return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
+  if (prec != HERMITE_FP64 && prec != HERMITE_FP32)
+    return fail(HERMITE_EUNSUPPORTED, "batched plans take FP64 or FP32 arithmetic, not %d", prec);
   if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
     return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
   if (prec == HERMITE_FP64 && state_dtype != HERMITE_STATE_FP64)

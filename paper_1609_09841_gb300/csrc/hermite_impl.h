@@ -60,6 +60,14 @@ StepCoeffs<T> cast_coeffs(const StepCoeffs<double> &in) {
   return o;
 }
 
+// Tables of the hybrid-precision kernel: the same tables in double, and as
+// double-float pairs (hi = float(d), lo = float(d - hi)).
+struct HybridCoeffs {
+  StepCoeffs<double> d;
+  StepCoeffs<float> hi;
+  StepCoeffs<float> lo;
+};
+
 // Grid geometry of one launch.
 struct Geom {
   int nx, ny, nz;
@@ -83,6 +91,12 @@ cudaError_t launch_fused_f32_s32(int m, int tile, const float *in, float *out, c
                                  const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
 cudaError_t launch_fused_f32_s64(int m, int tile, const double *in, double *out, const Geom &g,
                                  const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+
+// Hybrid-precision fused half step (FP64 state): kind 0 = grade-0 chain in
+// FP64, kind 1 = in double-float; `tile` < hybrid_tile_count().
+int hybrid_tile_count();
+cudaError_t launch_hybrid(int kind, int m, int tile, const double *in, double *out, const Geom &g,
+                          const HybridCoeffs &co, int zchunk, cudaStream_t st);
 
 // Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
 // output z-layers [z0, z0 + nzl); evolution reads it and writes the new node

@@ -24,6 +24,7 @@ struct hermite_plan_s {
   double H[64];
   hermite::StepCoeffs<double> fwd, adj, dc;
   hermite::StepCoeffs<float> fwd32, adj32, dc32;
+  hermite::HybridCoeffs hyb_fwd, hyb_adj, hyb_dc;
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
   int tile;                 // fused kernel: index of the compiled tile shape

@@ -67,6 +67,8 @@ int hermite_step_split_static(hermite_plan_t p, const void *in, void *out, int p
   if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
+  if (p->prec != HERMITE_FP64 && p->prec != HERMITE_FP32)
+    return fail(HERMITE_EUNSUPPORTED, "the split kernels have no hybrid precision");
   const size_t bytes = p->elems * (p->state == HERMITE_STATE_FP64 ? 8 : 4);
   const uintptr_t x = (uintptr_t)in, y = (uintptr_t)out;
   if (x < y + bytes && y < x + bytes) return fail(HERMITE_EINVAL, "input and output states overlap");

@@ -10,7 +10,8 @@ import numpy as np
 
 from . import capi
 
-PRECISIONS = {"fp64": capi.HERMITE_FP64, "fp32": capi.HERMITE_FP32}
+PRECISIONS = {"fp64": capi.HERMITE_FP64, "fp32": capi.HERMITE_FP32, "hybrid64": capi.HERMITE_HYBRID64,
+              "hybriddf": capi.HERMITE_HYBRIDDF}
 STATES = {"fp64": capi.HERMITE_STATE_FP64, "fp32": capi.HERMITE_STATE_FP32}
 VARIANTS = {"auto": capi.HERMITE_AUTO, "fused": capi.HERMITE_FUSED, "split": capi.HERMITE_SPLIT}
 

@@ -243,7 +243,8 @@ def test_standing_mode_config1_matches_oracle(torch_cuda):
 
 
 @pytest.mark.parametrize("m", [1, 2, 3])
-@pytest.mark.parametrize("prec,state", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "fp64")])
+@pytest.mark.parametrize("prec,state", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "fp64"),
+                                        ("hybrid64", "fp64"), ("hybriddf", "fp64")])
 def test_every_schedule_matches_oracle(torch_cuda, m, prec, state):
     """Every compiled tile shape, with z-chunks that leave a partial last
     chunk, on a grid with ragged tiles in x and y."""
@@ -256,7 +257,7 @@ def test_every_schedule_matches_oracle(torch_cuda, m, prec, state):
         x = x.astype(np.float32).astype(np.float64)
     xd = torch.from_numpy(x).cuda().to(plan.torch_dtype)
     yd = torch.empty_like(xd)
-    tol = 1e-12 if prec == "fp64" else 2e-5
+    tol = {"fp64": 1e-12, "fp32": 2e-5, "hybrid64": 1e-6, "hybriddf": 1e-6}[prec]
     for tile in range(capi.lib.hermite_schedule_count(plan.handle)):
         for zc in (1, 3, 16):
             capi.check(capi.lib.hermite_set_schedule(plan.handle, tile, zc))
@@ -265,3 +266,29 @@ def test_every_schedule_matches_oracle(torch_cuda, m, prec, state):
                 plan.step(xd, yd, parity)
                 ref = oracle.half_step(x, m, h, 1.0, dt, parity)
                 assert _relmax(yd.cpu().numpy().astype(np.float64), ref) <= tol, (tile, zc, parity)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["hybrid64", "hybriddf"])
+def test_hybrid_adjoint_and_dc(torch_cuda, m, prec):
+    """The hybrid modes' adjoint and dS/dc use the same split of the tables:
+    the adjoint against the oracle's transpose (1e-6, like the forward step),
+    dS/dc against a central difference of the oracle's step in c.  dS/dc has
+    no grade-0 term (its weights are 2s/c beta_s), so its dominant terms are
+    the FP32 ones and it carries the FP32 tolerance."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import Plan
+    n = GRIDS[m]
+    plan, h, dt = _plan(m, n, prec=prec, state="fp64")
+    g = HI.random_state(m, n, seed=80 + m)
+    gd = torch.from_numpy(g).cuda()
+    out = torch.empty_like(gd)
+    for parity in (0, 1):
+        plan.adjoint(gd, out, parity)
+        ref = oracle.adjoint_half_step(g, m, h, 1.0, dt, parity)
+        assert _relmax(out.cpu().numpy(), ref) <= 1e-6
+        plan.step_dc(gd, out, parity)
+        dc = 1e-4
+        a = oracle.half_step(g, m, h, 1.0 + dc, dt, parity)
+        b = oracle.half_step(g, m, h, 1.0 - dc, dt, parity)
+        assert _relmax(out.cpu().numpy(), (a - b) / (2 * dc)) <= 2e-5

@@ -11,7 +11,8 @@ Errors are relative max-norm (max|a-b| / max|b|) and relative L2 over every
 component of both fields, and separately over the values (orders 0) of u and
 of v; each test prints one JSON line per variant.
 
-The target for the mixed variants was 1e-5 relative at t = 1.  Measured, FP32
+The hybrid modes (grade-0 contractions in FP64 or double-float, the rest in
+FP32) must meet the stated bar of 1e-5 relative at t = 1.  Measured, FP32
 arithmetic meets it on the values of u at 64^3 and comes within 2x of it at
 256^3, but the derivative components and v carry a rounding error that grows
 linearly with the number of half steps (an O(eps32) perturbation of the
@@ -58,7 +59,8 @@ def _setup(n1):
     return m, n, h, dt, nhalf
 
 
-VARIANTS = [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32")]
+VARIANTS = [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("hybrid64", "fp64"), ("hybriddf", "fp64")]
+BAR = 1e-5       # the stated bar for the mixed variants at t = 1
 
 
 def test_mixed_vs_oracle_16(torch_cuda):
@@ -75,7 +77,7 @@ def test_mixed_vs_oracle_16(torch_cuda):
         print(json.dumps({"grid": 16, "nhalf": nhalf, "prec": prec, "state": state, "vs": "oracle",
                           "max_rel": mrel, "l2_rel": l2rel}))
         assert rc == 0
-        assert mrel <= (1e-12 if prec == "fp64" else GUARD[16])
+        assert mrel <= {"fp64": 1e-12, "fp32": GUARD[16]}.get(prec, BAR)
 
 
 @pytest.mark.parametrize("n1", [64, 256])
@@ -96,4 +98,4 @@ def test_mixed_vs_fp64_gpu(torch_cuda, n1):
                           "max_rel": mrel, "l2_rel": l2rel, "u_values_max_rel": mrelu, "u_values_l2_rel": l2relu,
                           "v_values_max_rel": mrelv, "v_values_l2_rel": l2relv}))
         assert rc == 0
-        assert mrel <= GUARD[n1]
+        assert mrel <= (GUARD[n1] if prec == "fp32" else BAR)
