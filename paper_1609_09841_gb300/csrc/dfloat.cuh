@@ -25,9 +25,20 @@ __device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {  // requires
   return {s, b - (s - a)};
 }
 
+// Split a double into hi + lo without FP64 arithmetic: hi keeps the top 24
+// significand bits (exact in FP32), lo the remaining 29 bits rounded to FP32
+// (scaled by the exponent; values below 2^-74 keep hi only).  The pair is
+// accurate to about 2^-47 relative.
 __device__ __forceinline__ df32 df_from(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
+  const long long b = __double_as_longlong(x);
+  const float hi = __double2float_rn(__longlong_as_double(b & ~0x1FFFFFFFLL));
+  const int e = (int)((b >> 52) & 0x7FF) - 1075;  // weight of the last significand bit is 2^e
+  float lo = 0.f;
+  if (e >= -126) {
+    lo = (float)(int)(b & 0x1FFFFFFFLL) * __int_as_float((e + 127) << 23);
+    if (b < 0) lo = -lo;
+  }
+  return {hi, lo};
 }
 
 __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
@@ -40,7 +51,30 @@ __device__ __forceinline__ df32 operator+(df32 a, df32 b) {
 
 __device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + df32{-b.hi, -b.lo}; }
 
-// acc + c * x
+// Renormalise a pair whose lo may have grown (|hi| >= |lo| holds).
+__device__ __forceinline__ df32 df_norm(df32 a) { return df_fast_two_sum(a.hi, a.lo); }
+
+// acc + c * x without renormalisation (acc.lo accumulates the low parts; call
+// df_norm at the end of a short chain).
+__device__ __forceinline__ df32 df_mad(df32 c, df32 x, df32 acc) {
+  const float p = c.hi * x.hi;
+  float e = fmaf(c.hi, x.hi, -p);
+  e = fmaf(c.hi, x.lo, e);
+  e = fmaf(c.lo, x.hi, e);
+  const df32 s = df_two_sum(acc.hi, p);
+  return {s.hi, s.lo + (acc.lo + e)};
+}
+
+// The same with a coefficient exact in FP32.
+__device__ __forceinline__ df32 df_mad1(float c, df32 x, df32 acc) {
+  const float p = c * x.hi;
+  float e = fmaf(c, x.hi, -p);
+  e = fmaf(c, x.lo, e);
+  const df32 s = df_two_sum(acc.hi, p);
+  return {s.hi, s.lo + (acc.lo + e)};
+}
+
+// acc + c * x, renormalised
 __device__ __forceinline__ df32 df_fma(df32 c, df32 x, df32 acc) {
   const float p = c.hi * x.hi;
   float e = fmaf(c.hi, x.hi, -p);

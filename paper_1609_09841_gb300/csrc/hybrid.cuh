@@ -31,6 +31,9 @@ struct HiF64 {  // high-precision part in FP64
   static __device__ __forceinline__ float to_float(T x) { return (float)x; }
   static __device__ __forceinline__ T zero() { return 0.0; }
   static __device__ __forceinline__ T mad(T c, T x, T acc) { return ::fma(c, x, acc); }
+  static __device__ __forceinline__ T mad_exact(double c, float, T x, T acc) { return ::fma(c, x, acc); }
+  static __device__ __forceinline__ T norm(T x) { return x; }
+  static __device__ __forceinline__ double to_double_plus(T x, float f) { return x + (double)f; }
   static __device__ __forceinline__ T gx(const HybridCoeffs &c, int a, int q) { return c.d.gx[a][q]; }
   static __device__ __forceinline__ T gy(const HybridCoeffs &c, int b, int q) { return c.d.gy[b][q]; }
   static __device__ __forceinline__ T kz(const HybridCoeffs &c, int fo, int fi, int q) { return c.d.kz[fo][fi][0][q]; }
@@ -42,7 +45,11 @@ struct HiDF {  // high-precision part in double-float
   static __device__ __forceinline__ double to_double(T x) { return df_to_double(x); }
   static __device__ __forceinline__ float to_float(T x) { return df_to_float(x); }
   static __device__ __forceinline__ T zero() { return df32{0.f, 0.f}; }
-  static __device__ __forceinline__ T mad(T c, T x, T acc) { return df_fma(c, x, acc); }
+  static __device__ __forceinline__ T mad(T c, T x, T acc) { return df_mad(c, x, acc); }
+  // G_0 = T1 H has dyadic entries with numerators <= 35: exact in FP32, no low word
+  static __device__ __forceinline__ T mad_exact(double, float c, T x, T acc) { return df_mad1(c, x, acc); }
+  static __device__ __forceinline__ T norm(T x) { return df_norm(x); }
+  static __device__ __forceinline__ double to_double_plus(T x, float f) { return df_to_double(x + df32{f, 0.f}); }
   static __device__ __forceinline__ T gx(const HybridCoeffs &c, int a, int q) { return {c.hi.gx[a][q], c.lo.gx[a][q]}; }
   static __device__ __forceinline__ T gy(const HybridCoeffs &c, int b, int q) { return {c.hi.gy[b][q], c.lo.gy[b][q]}; }
   static __device__ __forceinline__ T kz(const HybridCoeffs &c, int fo, int fi, int q) {
@@ -170,7 +177,14 @@ __global__ void __launch_bounds__(NT)
         for (int r = 0; r < M; ++r) {
           H acc = Hi::zero();
 #pragma unroll
-          for (int i = 0; i < M; ++i) acc = Hi::mad(Hi::gx(co, a, r * 4 + i), (r & 1) ? dv[i] : sv[i], acc);
+          for (int i = 0; i < M; ++i) {
+            const int q = r * 4 + i;
+            if (a == 0)
+              acc = Hi::mad_exact(co.d.gx[0][q], co.hi.gx[0][q], (r & 1) ? dv[i] : sv[i], acc);
+            else
+              acc = Hi::mad(Hi::gx(co, a, q), (r & 1) ? dv[i] : sv[i], acc);
+          }
+          acc = Hi::norm(acc);
           if (a == 0)
             sX0[xd0[k] + r * XS] = acc;
           else
@@ -207,7 +221,14 @@ __global__ void __launch_bounds__(NT)
           H acc = Hi::zero();
           if (gg < NA) {
 #pragma unroll
-            for (int i = 0; i < M; ++i) acc = Hi::mad(Hi::gy(co, gg, r * 4 + i), (r & 1) ? d0[i] : s0[i], acc);
+            for (int i = 0; i < M; ++i) {
+              const int q = r * 4 + i;
+              if (gg == 0)
+                acc = Hi::mad_exact(co.d.gy[0][q], co.hi.gy[0][q], (r & 1) ? d0[i] : s0[i], acc);
+              else
+                acc = Hi::mad(Hi::gy(co, gg, q), (r & 1) ? d0[i] : s0[i], acc);
+            }
+            acc = Hi::norm(acc);
           }
           if (gg == 0) {
             y0o[r * M * YS] = acc;
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(NT)
                 for (int i = 0; i < M; ++i)
                   accf = fmaf(co.hi.kz[fo][fi][gm + 1][r * 4 + i], (r & 1) ? d1[fi][gm][i] : s1[fi][gm][i], accf);
             }
-            o[(size_t)((fo * M + r) * M * M) * plane] = Hi::to_double(acc) + (double)accf;
+            o[(size_t)((fo * M + r) * M * M) * plane] = Hi::to_double_plus(Hi::norm(acc), accf);
           }
       }
     }
