@@ -131,6 +131,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(dist, v, device):
+    """Largest of the ranks' values (all ranks get it); v itself without a process group."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, dof_per_rank, ms_max):
+    """Whole-job throughput of independent replicas: every rank advances its
+    own grid of dof_per_rank values per half step; the job is as slow as its
+    slowest rank."""
+    return world * dof_per_rank / (ms_max * 1e-3)
+
+
+def fixed_or_tuned(args, plan, x, y, zchunks=(8, 16, 32, 64), reps=2):
+    """--tile fixes every leg's schedule (profiling runs); otherwise autotune."""
+    from paper_1609_09841_gb300.autotune import tune
+    if args.tile >= 0:
+        plan.set_schedule(min(args.tile, plan.schedule_count() - 1), args.zchunk)
+        return {"tile": args.tile, "zchunk": args.zchunk, "ms": None}
+    return tune(plan, x, y, zchunks=zchunks, reps=reps, cache=None)
+
+
 def timed_steps(torch, plan, x, y, steps, warmup):
     """W untimed then K timed half steps (alternating parity), CUDA events on
     the launching stream; returns ms per step."""
@@ -172,12 +198,8 @@ def run_ours(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_over_ranks(v):  # noqa: F811 (rank-local shorthand)
+        return globals()["max_over_ranks"](dist, v, "cuda")
 
     # mixed precision: FP32 arithmetic, FP32 state
     plan = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp32")
@@ -186,20 +208,26 @@ def run_ours(args, rank, world):
     if args.tile >= 0:
         plan.set_schedule(args.tile, args.zchunk)
         sched = {"mixed": {"tile": args.tile, "zchunk": args.zchunk, "ms": None}}
-    else:
+    elif "mixed" in legs:
         sched = {"mixed": tune(plan, x, y, cache=None)}
+    else:
+        sched = {}
     x = torch.randn(plan.shape, dtype=torch.float32, device="cuda", generator=gen)
-    for k in range(args.warmup):
-        plan.step(x, y, k % 2)
-        x, y = y, x
     clocks = ClockSampler()
-    barrier()
-    clocks.start()
-    ms = timed_steps(torch, plan, x, y, args.steps, 0)
+    ms = float("nan")
+    if "mixed" in legs:
+        for k in range(args.warmup):
+            plan.step(x, y, k % 2)
+            x, y = y, x
+        barrier()
+        clocks.start()
+        ms = timed_steps(torch, plan, x, y, args.steps, 0)
+    else:
+        clocks.start()
     clk = clocks.stop()
     barrier()
     ms_max = max_over_ranks(ms)
-    value = world * dof / (ms_max * 1e-3)
+    value = replica_value(world, dof, ms_max)
     traffic_alg = plan.elems * 4 * 2          # read + write of the FP32 state
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -213,18 +241,18 @@ def run_ours(args, rank, world):
         yd = torch.empty_like(xd)
         if "mixed64" in legs:   # same arithmetic, FP64 state (loaded, computed in FP32, stored)
             plan64s = Plan(m, n, h, 1.0, dt, prec="fp32", state="fp64")
-            sched["mixed64"] = tune(plan64s, xd, yd, cache=None)
+            sched["mixed64"] = fixed_or_tuned(args, plan64s, xd, yd)
             xd.copy_(x)
             ms_mixed64 = timed_steps(torch, plan64s, xd, yd, args.steps, args.warmup)
         for hk in ("hybriddf", "hybrid64"):   # FP64 state, grade-0 contractions in double-float / FP64
             if hk in legs:
                 planh = Plan(m, n, h, 1.0, dt, prec=hk, state="fp64")
-                sched[hk] = tune(planh, xd, yd, zchunks=(16, 32, 64), reps=1, cache=None)
+                sched[hk] = fixed_or_tuned(args, planh, xd, yd, zchunks=(16, 32, 64), reps=1)
                 xd.copy_(x)
                 ms_hyb[hk] = timed_steps(torch, planh, xd, yd, max(3, args.steps // 4), min(args.warmup, 3))
         if "fp64" in legs:      # plain FP64
             plan64 = Plan(m, n, h, 1.0, dt, prec="fp64", state="fp64")
-            sched["fp64"] = tune(plan64, xd, yd, zchunks=(16, 32), reps=1, cache=None)
+            sched["fp64"] = fixed_or_tuned(args, plan64, xd, yd, zchunks=(16, 32), reps=1)
             xd.copy_(x)
             ms64 = timed_steps(torch, plan64, xd, yd, args.fp64_steps, min(args.warmup, 3))
         del xd, yd
@@ -276,7 +304,7 @@ def run_ours(args, rank, world):
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                      "flop_per_node": flop_node, "hbm_achieved_gbs": achieved, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": achieved / hbm_peak, "hbm_peak_source": "measured (MEASURED_PEAKS.json)",
-                     "kernel": f"fused_step_kernel<float, float, {m + 1}, ...> (schedule {sched['mixed']['tile']})"},
+                     "kernel": f"fused_step_kernel<float, float, {m + 1}, ...> (schedule {sched.get('mixed', {}).get('tile')})"},
         "fp64": {"value": world * dof / (max_over_ranks(ms64) * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps,
                  "dtype": "f64", "state": "fp64",
                  "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
