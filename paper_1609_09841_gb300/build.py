@@ -15,7 +15,8 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhermite.so")
 SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + \
+    os.environ.get("HERMITE_NVCC_FLAGS", "").split()
 
 
 def nvcc():

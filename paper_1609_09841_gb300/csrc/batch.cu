@@ -18,6 +18,10 @@ template <> struct BatchTile<2> { static constexpr int TX = 8, TY = 8; };
 template <> struct BatchTile<3> { static constexpr int TX = 8, TY = 4; };
 template <> struct BatchTile<4> { static constexpr int TX = 4, TY = 4; };
 constexpr int kBatchThreads = 256;
+// Resident CTAs per SM the compiler must fit the batched kernel's registers to.
+#ifndef HERMITE_BATCH_MIN_BLOCKS
+#define HERMITE_BATCH_MIN_BLOCKS 1
+#endif
 
 void batch_tile_shape(int m, int *tx, int *ty) {
   switch (m) {
@@ -52,7 +56,7 @@ __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &
 }
 
 template <typename TS, typename TC>
-__global__ void __launch_bounds__(kBatchThreads)
+__global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
     batch_step_kernel(const BatchSim *__restrict__ sims, const StepCoeffs<TC> *__restrict__ coeffs,
                       const BatchItem *__restrict__ items, int nitems, int *__restrict__ counter, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
