@@ -82,6 +82,8 @@ Geom geom_of(const hermite_plan_s *p, int s) {
   g.ny = p->n[1];
   g.nz = p->n[2];
   g.s = s;
+  g.zlo = 0;
+  g.zhi = g.nz;
   return g;
 }
 
@@ -122,11 +124,16 @@ int ensure_red(hermite_plan_s *p) {
 
 // Device-pointer half step of either direction (adjoint: transposed tables,
 // mirrored corner offset).
-int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st) {
+int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st, int zlo = 0,
+             int zhi = -1) {
   const int s_fwd = parity == 0 ? 0 : -1;
   const bool adjoint = mode == kAdjoint;
   const int s = adjoint ? -s_fwd - 1 : s_fwd;
-  const Geom g = geom_of(p, s);
+  Geom g = geom_of(p, s);
+  if (zhi >= 0) {
+    g.zlo = zlo;
+    g.zhi = zhi;
+  }
   const bool split = p->variant == HERMITE_SPLIT && mode == kForward;
   cudaError_t e = cudaSuccess;
   if (!split) {
@@ -164,6 +171,83 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     e = launch_evolve(p->m, state, compute, p->ws, out, g, z0, nl, p->evolve, st);
     if (e != cudaSuccess) return cuda_fail(e, "evolution kernel launch");
   }
+  return HERMITE_OK;
+}
+
+// z planes [a, b) (wrapping modulo nz) of every component, between a host and
+// a device state: one strided copy per contiguous run.
+int copy_planes(hermite_plan_s *p, void *dst, const void *src, int a, int b, cudaMemcpyKind kind,
+                cudaStream_t st) {
+  const int nz = p->n[2];
+  const size_t elt = p->state == HERMITE_STATE_FP64 ? sizeof(double) : sizeof(float);
+  const size_t pxy = (size_t)p->n[0] * p->n[1] * elt, plane = pxy * nz;
+  const size_t ncomp = p->elems / ((size_t)p->n[0] * p->n[1] * nz);
+  while (a < b) {
+    const int za = ((a % nz) + nz) % nz;
+    const int len = std::min(b - a, nz - za);
+    cudaError_t e = cudaMemcpy2DAsync((char *)dst + za * pxy, plane, (const char *)src + za * pxy, plane, len * pxy,
+                                      ncomp, kind, st);
+    if (e != cudaSuccess) return cuda_fail(e, "state slab copy");
+    a += len;
+  }
+  return HERMITE_OK;
+}
+
+// Host-buffer half step, pipelined over z-slabs: the copy of slab k+1 in, the
+// half step of slab k and the copy of slab k-1 out overlap on three streams.
+// Output layers [zb_k, zb_k+1) read input planes zb_k + s .. zb_k+1 + s, i.e.
+// slab k's planes and the first plane of slab k+1.
+int host_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaStream_t st) {
+  const size_t bytes = state_bytes(p);
+  if (overlaps(in, out, bytes)) return fail(HERMITE_EINVAL, "input and output states overlap");
+  for (int k = 0; k < 2; ++k)
+    if (!p->stage[k]) {
+      cudaError_t e = cudaMalloc(&p->stage[k], bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->stage[k] = nullptr;
+        return fail(HERMITE_ENOMEM, "staging buffer of %zu bytes", bytes);
+      }
+    }
+  if (!p->copy_in) {
+    cudaError_t e = cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking);
+    for (auto &ev : p->ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "copy streams");
+  }
+  const int nz = p->n[2];
+  const int K = p->variant == HERMITE_SPLIT ? 1 : std::min(nz, 16);
+  const int s = parity == 0 ? 0 : -1;
+  cudaEvent_t *ein = p->ev, *eout = p->ev + 16, start = p->ev[32], done = p->ev[33];
+  cudaError_t e = cudaEventRecord(start, st);  // order after earlier work on the caller's stream
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_in, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_out, start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+  auto zb = [&](int k) { return (int)((long long)k * nz / K); };
+  for (int k = 0; k < K; ++k) {
+    int rc = copy_planes(p, p->stage[0], in, zb(k) + s, zb(k + 1) + s, cudaMemcpyHostToDevice, p->copy_in);
+    if (rc) return rc;
+    e = cudaEventRecord(ein[k], p->copy_in);
+    if (e != cudaSuccess) return cuda_fail(e, "event");
+  }
+  for (int k = 0; k < K; ++k) {
+    e = cudaStreamWaitEvent(st, ein[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ein[(k + 1) % K], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    int rc = K == 1 ? run_step(p, p->stage[0], p->stage[1], parity, kForward, st)
+                    : run_step(p, p->stage[0], p->stage[1], parity, kForward, st, zb(k), zb(k + 1));
+    if (rc) return rc;
+    e = cudaEventRecord(eout[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_out, eout[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+    rc = copy_planes(p, out, p->stage[1], zb(k), zb(k + 1), cudaMemcpyDeviceToHost, p->copy_out);
+    if (rc) return rc;
+  }
+  e = cudaEventRecord(done, p->copy_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "host-buffer step");
   return HERMITE_OK;
 }
 
@@ -286,27 +370,7 @@ int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *
     if (rc) return rc;
     return run_step(p, in, out, parity, kForward, st);
   }
-  // Host buffers: copy in, step, copy out through plan-owned device buffers.
-  const size_t bytes = state_bytes(p);
-  if (overlaps(in, out, bytes)) return fail(HERMITE_EINVAL, "input and output states overlap");
-  for (int k = 0; k < 2; ++k)
-    if (!p->stage[k]) {
-      cudaError_t e = cudaMalloc(&p->stage[k], bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        p->stage[k] = nullptr;
-        return fail(HERMITE_ENOMEM, "staging buffer of %zu bytes", bytes);
-      }
-    }
-  cudaError_t e = cudaMemcpyAsync(p->stage[0], in, bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
-  int rc = run_step(p, p->stage[0], p->stage[1], parity, kForward, st);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(out, p->stage[1], bytes, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
-  return HERMITE_OK;
+  return host_step(p, in, out, parity, st);
 }
 
 int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, int parity, void *stream) {
@@ -400,6 +464,10 @@ int hermite_dot(hermite_plan_t p, const void *a, const void *b, double *out, voi
 
 void hermite_destroy(hermite_plan_t p) {
   if (!p) return;
+  for (auto &ev : p->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (p->copy_in) cudaStreamDestroy(p->copy_in);
+  if (p->copy_out) cudaStreamDestroy(p->copy_out);
   if (p->batch) destroy_batch(p->batch);
   if (p->ws) cudaFree(p->ws);
   for (int k = 0; k < 2; ++k)

@@ -20,7 +20,7 @@ template <> struct BatchTile<4> { static constexpr int TX = 4, TY = 4; };
 constexpr int kBatchThreads = 256;
 // Resident CTAs per SM the compiler must fit the batched kernel's registers to.
 #ifndef HERMITE_BATCH_MIN_BLOCKS
-#define HERMITE_BATCH_MIN_BLOCKS 1
+#define HERMITE_BATCH_MIN_BLOCKS 2
 #endif
 
 void batch_tile_shape(int m, int *tx, int *ty) {
@@ -49,6 +49,8 @@ __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &
   g.ny = sm.n[1];
   g.nz = sm.n[2];
   g.s = s;
+  g.zlo = 0;
+  g.zhi = g.nz;
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
   const int z0 = it.z0, z1 = min(it.z0 + sm.zchunk, g.nz);

@@ -25,44 +25,23 @@ __device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {  // requires
   return {s, b - (s - a)};
 }
 
-// The float holding the top 24 significand bits of a double (truncation),
-// composed with integer operations.  Values below 2^-126 give 0 (their low
-// word is dropped too); values must be below 2^128.
-__device__ __forceinline__ float df_trunc_hi(long long b) {
-  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-  if (e <= 0) return 0.f;
-  const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
-  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
-}
-
-// The double equal to a normal float, composed with integer operations
-// (zero and subnormal floats give 0).
-__device__ __forceinline__ double df_widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFF;
-  if (e == 0) return 0.0;
-  return __longlong_as_double(((unsigned long long)(u >> 31) << 63) |
-                              ((unsigned long long)(e - 127 + 1023) << 52) |
-                              ((unsigned long long)(u & 0x7FFFFF) << 29));
-}
-
-// Split a double into hi + lo without FP64 instructions: hi keeps the top 24
+// Split a double into hi + lo without FP64 arithmetic: hi keeps the top 24
 // significand bits (exact in FP32), lo the remaining 29 bits rounded to FP32
 // (scaled by the exponent; values below 2^-74 keep hi only).  The pair is
 // accurate to about 2^-47 relative.
 __device__ __forceinline__ df32 df_from(double x) {
   const long long b = __double_as_longlong(x);
-  const float hi = df_trunc_hi(b);
+  const float hi = __double2float_rn(__longlong_as_double(b & ~0x1FFFFFFFLL));
   const int e = (int)((b >> 52) & 0x7FF) - 1075;  // weight of the last significand bit is 2^e
   float lo = 0.f;
   if (e >= -126) {
-    lo = (float)(int)(b & 0x1FFFFFFFLL) * __uint_as_float((unsigned)(e + 127) << 23);
+    lo = (float)(int)(b & 0x1FFFFFFFLL) * __int_as_float((e + 127) << 23);
     if (b < 0) lo = -lo;
   }
   return {hi, lo};
 }
 
-__device__ __forceinline__ double df_to_double(df32 a) { return df_widen(a.hi) + df_widen(a.lo); }
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ float df_to_float(df32 a) { return a.hi + a.lo; }
 
 __device__ __forceinline__ df32 operator+(df32 a, df32 b) {

@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(NT)
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (blockIdx.x % tiles_x) * TX;
   const int y0 = (blockIdx.x / tiles_x) * TY;
-  const int z0 = blockIdx.y * zchunk;
-  if (z0 >= g.nz) return;
-  fused_tile<TS, TC, M, TX, TY, NT>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.nz), co, sX, sY);
+  const int z0 = g.zlo + blockIdx.y * zchunk;
+  if (z0 >= g.zhi) return;
+  fused_tile<TS, TC, M, TX, TY, NT>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
 }
 
 template <typename TS, typename TC, int M, int TX, int TY, int NT>
@@ -252,7 +252,7 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
   }
   if (zchunk <= 0) zchunk = 16;
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-  dim3 grid(tiles, (g.nz + zchunk - 1) / zchunk);
+  dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
   kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co);
   return cudaGetLastError();
 }

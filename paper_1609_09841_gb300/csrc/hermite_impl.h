@@ -71,7 +71,8 @@ struct HybridCoeffs {
 // Grid geometry of one launch.
 struct Geom {
   int nx, ny, nz;
-  int s;  // corner offset: corners of output node o are o + s + {0, 1} per dimension
+  int s;         // corner offset: corners of output node o are o + s + {0, 1} per dimension
+  int zlo, zhi;  // output z layers [zlo, zhi) computed by a launch (the fused and hybrid kernels)
 };
 
 // Launch configuration of the fused kernel (chosen per m and precision).

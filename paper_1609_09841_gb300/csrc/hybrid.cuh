@@ -92,9 +92,9 @@ __global__ void __launch_bounds__(NT)
   const int tiles_x = (nx + TX - 1) / TX;
   const int x0 = (blockIdx.x % tiles_x) * TX;
   const int y0 = (blockIdx.x / tiles_x) * TY;
-  const int z0 = blockIdx.y * zchunk;
-  if (z0 >= nz) return;
-  const int z1 = min(z0 + zchunk, nz);
+  const int z0 = g.zlo + blockIdx.y * zchunk;
+  if (z0 >= g.zhi) return;
+  const int z1 = min(z0 + zchunk, g.zhi);
   const size_t pxy = (size_t)nx * ny;
   const size_t plane = pxy * nz;
 
@@ -309,7 +309,7 @@ cudaError_t launch_hybrid_cfg(const double *in, double *out, const Geom &g, cons
   }
   if (zchunk <= 0) zchunk = 16;
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-  dim3 grid(tiles, (g.nz + zchunk - 1) / zchunk);
+  dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
   kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co);
   return cudaGetLastError();
 }

@@ -36,4 +36,6 @@ struct hermite_plan_s {
   double *red = nullptr;    // error reduction scratch (device)
   double *red_host = nullptr;  // pinned result
   hermite::BatchPlan *batch = nullptr;  // set for batched plans (hermite_batch_plan)
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer steps: copy streams
+  cudaEvent_t ev[2 * 16 + 2] = {};                     // host-buffer steps: chunk events
 };

@@ -176,42 +176,21 @@ __global__ void __launch_bounds__(NT)
     (f ? wv : wu)[cb * P3 + j] = v;
   }
   __syncthreads();
-  // Each thread owns the same coefficients in every Horner stage: their
-  // second-derivative factors c^2/h_k^2 (j_k+1)(j_k+2) (zero past the top
-  // index) are formed once, before the stages.
-  constexpr int EPT = (CB * P3 + NT - 1) / NT;
-  TC fx[EPT], fy[EPT], fz[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = threadIdx.x + q * NT;
-    const int j = e % P3;
-    const int jx = j % P, jy = (j / P) % P, jz = j / (P * P);
-    fx[q] = jx + 2 < P ? (TC)(ep.c2h[0] * ((jx + 1) * (jx + 2))) : (TC)0;
-    fy[q] = jy + 2 < P ? (TC)(ep.c2h[1] * ((jy + 1) * (jy + 2))) : (TC)0;
-    fz[q] = jz + 2 < P ? (TC)(ep.c2h[2] * ((jz + 1) * (jz + 2))) : (TC)0;
-  }
+  const TC c2h[3] = {(TC)ep.c2h[0], (TC)ep.c2h[1], (TC)ep.c2h[2]};
   for (int k = 4; k >= 1; --k) {
     const TC a = (TC)(ep.tau / k);
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (e >= CB * P3) continue;
+    for (int e = threadIdx.x; e < CB * P3; e += NT) {
       const int cb = e / P3, j = e - cb * P3;
+      const int jx = j % P, jy = (j / P) % P, jz = j / (P * P);
       const TC *w = wu + cb * P3;
-      // a factor is zero exactly when j_k + 2 is past the top index: the read
-      // of that neighbour is skipped
       TC lap = 0;
-      if (fx[q] != (TC)0) lap = fma(fx[q], w[j + 2], lap);
-      if (fy[q] != (TC)0) lap = fma(fy[q], w[j + 2 * P], lap);
-      if (fz[q] != (TC)0) lap = fma(fz[q], w[j + 2 * P * P], lap);
+      if (jx + 2 < P) lap = fma(c2h[0] * (TC)((jx + 1) * (jx + 2)), w[j + 2], lap);
+      if (jy + 2 < P) lap = fma(c2h[1] * (TC)((jy + 1) * (jy + 2)), w[j + 2 * P], lap);
+      if (jz + 2 < P) lap = fma(c2h[2] * (TC)((jz + 1) * (jz + 2)), w[j + 2 * P * P], lap);
       tv[e] = fma(a, lap, yv[e]);
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = threadIdx.x + q * NT;
-      if (e < CB * P3) wu[e] = fma(a, wv[e], yu[e]);
-    }
+    for (int e = threadIdx.x; e < CB * P3; e += NT) wu[e] = fma(a, wv[e], yu[e]);
     __syncthreads();
     TC *t = wv;
     wv = tv;

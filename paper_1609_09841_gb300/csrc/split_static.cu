@@ -90,6 +90,8 @@ int hermite_step_split_static(hermite_plan_t p, const void *in, void *out, int p
   g.ny = p->n[1];
   g.nz = p->n[2];
   g.s = parity == 0 ? 0 : -1;
+  g.zlo = 0;
+  g.zhi = g.nz;
   const int compute = p->prec == HERMITE_FP64 ? kF64 : kF32;
   const int state = p->state == HERMITE_STATE_FP64 ? kF64 : kF32;
   cudaStream_t st = (cudaStream_t)stream;

@@ -99,18 +99,24 @@ def test_gpu_dot_product_identity(torch_cuda):
         assert abs(lhs - rhs) <= 1e-13 * float(sx.norm() * y.norm())
 
 
-def test_host_buffer_step_equals_device_step(torch_cuda):
+@pytest.mark.parametrize("prec,state,variant", [("fp64", "fp64", "fused"), ("fp32", "fp32", "fused"),
+                                                ("hybriddf", "fp64", "fused"), ("fp64", "fp64", "split")])
+def test_host_buffer_step_equals_device_step(torch_cuda, prec, state, variant):
+    """Host buffers go through the z-slab pipeline (copy in, step, copy out on
+    three streams); the result must equal the device-buffer step bit for bit,
+    on both parities (the dual->primal one reads a wrapped plane)."""
     torch = torch_cuda
     m, n = 2, (9, 8, 7)
-    for state in ("fp64", "fp32"):
-        plan, h, dt = _plan(m, n, prec="fp32" if state == "fp32" else "fp64", state=state)
-        x = HI.random_state(m, n, seed=8).astype(np.float64 if state == "fp64" else np.float32)
-        y_host = np.empty_like(x)
-        plan.step(x, y_host, 1)
-        xd = torch.from_numpy(x).cuda()
-        yd = torch.empty_like(xd)
-        plan.step(xd, yd, 1)
-        assert np.array_equal(y_host, yd.cpu().numpy())
+    plan, h, dt = _plan(m, n, prec=prec, state=state, variant=variant)
+    x = HI.random_state(m, n, seed=8).astype(np.float64 if state == "fp64" else np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    for parity in (0, 1):
+        y_host = np.full_like(x, np.nan)
+        plan.step(x, y_host, parity)
+        plan.step(xd, yd, parity)
+        torch.cuda.synchronize()
+        assert np.array_equal(y_host, yd.cpu().numpy()), parity
 
 
 def test_invalid_buffers_rejected(torch_cuda):
