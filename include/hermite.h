@@ -214,6 +214,17 @@ int hermite_step_split_static(hermite_plan_t plan, const void *in_state, void *o
 /* HERMITE_STATIC_WORKSPACE_BYTES, as compiled into the library. */
 size_t hermite_static_workspace_bytes(void);
 
+/* Number of Taylor stages q of the local evolution (Alg. 4, Sec. 3.2).  The
+ * default q = 4 is classical RK4 (the same polynomial in tau L).  Up to
+ * q = 3(2m+1) = d(2N+1) stages the series is exact for the cell polynomial
+ * (the paper's choice for the largest stable step; the library's stability
+ * check stays the one of q = 4, which is the more restrictive).  Rebuilds the
+ * plan's tables; the fused kernel then carries more grades of the series.
+ * EINVAL outside 4..3(2m+1); EUNSUPPORTED for the hybrid precisions (4 only).
+ * Batched plans always use q = 4. */
+int hermite_set_taylor_order(hermite_plan_t plan, int q);
+int hermite_taylor_order(hermite_plan_t plan);
+
 /* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
 size_t hermite_state_elems(hermite_plan_t plan);
 

@@ -190,9 +190,10 @@ def evolve_taylor(Bu, Bv, tau, c, h, q=4):
 # ---------------------------------------------------------------------------
 
 
-def cell_map(U, m, h, c, tau, evolve="rk4"):
+def cell_map(U, m, h, c, tau, evolve="rk4", q=4):
     """Map a batch of local tensors (ncell, 2, P, P, P) to the new node data
-    (ncell, 2, M, M, M) [cell, f, i3, i2, i1]."""
+    (ncell, 2, M, M, M) [cell, f, i3, i2, i1].  evolve = "rk4" (classical
+    RK4), "taylor" (Alg. 4 with q stages) or "none"."""
     M = m + 1
     H = hermite_matrix(m)
     R = reconstruct(U, H)
@@ -200,7 +201,7 @@ def cell_map(U, m, h, c, tau, evolve="rk4"):
     if evolve == "rk4":
         Bu, Bv = evolve_rk4(Bu, Bv, tau, c, h)
     elif evolve == "taylor":
-        Bu, Bv = evolve_taylor(Bu, Bv, tau, c, h)
+        Bu, Bv = evolve_taylor(Bu, Bv, tau, c, h, q)
     elif evolve == "none":
         pass
     else:
@@ -208,7 +209,7 @@ def cell_map(U, m, h, c, tau, evolve="rk4"):
     return np.stack([Bu[:, :M, :M, :M], Bv[:, :M, :M, :M]], axis=1)
 
 
-def half_step(S, m, h, c, dt, parity, evolve="rk4", z_cells=None, chunk_cells=8192):
+def half_step(S, m, h, c, dt, parity, evolve="rk4", z_cells=None, chunk_cells=8192, q=4):
     """One half step of the whole grid (vectorised over cells).
 
     ``z_cells`` restricts the output to those z layers (the rest of the
@@ -226,16 +227,16 @@ def half_step(S, m, h, c, dt, parity, evolve="rk4", z_cells=None, chunk_cells=81
     for k in range(0, len(zs), per):
         zc = zs[k:k + per]
         U = gather_cells(S, m, parity, zc)
-        V = cell_map(U, m, h, c, tau, evolve)             # (ncell, 2, M, M, M)
+        V = cell_map(U, m, h, c, tau, evolve, q)          # (ncell, 2, M, M, M)
         out[..., zc, :, :] = V.reshape(len(zc), ny, nx, 2, M, M, M).transpose(3, 4, 5, 6, 0, 1, 2)
     return out
 
 
-def run(S, m, h, c, dt, nhalf, parity0=0, evolve="rk4"):
+def run(S, m, h, c, dt, nhalf, parity0=0, evolve="rk4", q=4):
     """nhalf half steps alternating primal->dual and dual->primal (Sec. 2)."""
     p = parity0
     for _ in range(nhalf):
-        S = half_step(S, m, h, c, dt, p, evolve)
+        S = half_step(S, m, h, c, dt, p, evolve, q=q)
         p ^= 1
     return S
 
@@ -325,14 +326,14 @@ def half_step_literal(S, m, h, c, dt, parity):
 # ---------------------------------------------------------------------------
 
 
-def cell_matrix(m, h, c, dt, evolve="rk4"):
+def cell_matrix(m, h, c, dt, evolve="rk4", q=4):
     """Dense per-cell matrix W (2 M^3 x 2 P^3) of the half step, built by
     applying the per-cell map to unit local tensors.  Column index (f, tz, ty,
     tx), row index (f, i3, i2, i1)."""
     M, P = m + 1, 2 * m + 2
     n_in = 2 * P ** 3
     E = np.eye(n_in).reshape(n_in, 2, P, P, P)
-    out = cell_map(E, m, h, c, 0.5 * dt, evolve)
+    out = cell_map(E, m, h, c, 0.5 * dt, evolve, q)
     return out.reshape(n_in, 2 * M ** 3).T.copy()
 
 
@@ -364,7 +365,7 @@ def half_step_matrix_form(S, m, h, c, dt, parity):
     return out.reshape(S.shape)
 
 
-def adjoint_half_step(G, m, h, c, dt, parity):
+def adjoint_half_step(G, m, h, c, dt, parity, evolve="rk4", q=4):
     """Transpose of the half step of the given parity: for an output-grid
     cotangent G, returns the input-grid cotangent sum over the 8 cells that
     contain each node of W_abc^T G(cell)."""
@@ -373,7 +374,7 @@ def adjoint_half_step(G, m, h, c, dt, parity):
     n = G.shape[-3:]
     Gf = G.reshape((2 * M ** 3,) + n)
     out = np.zeros((2 * M ** 3, int(np.prod(n))))
-    for (a, b, cc), Wb in corner_blocks(cell_matrix(m, h, c, dt), m).items():
+    for (a, b, cc), Wb in corner_blocks(cell_matrix(m, h, c, dt, evolve, q), m).items():
         sh = np.roll(Gf, shift=(s + cc, s + b, s + a), axis=(1, 2, 3))
         out += Wb.T @ sh.reshape(2 * M ** 3, -1)
     return out.reshape(G.shape)

@@ -26,13 +26,13 @@ def symbol(m, h, c, dt, theta):
     return G
 
 
-def max_spectral_radius(m, lam, npts=7, dims=3):
+def max_spectral_radius(m, lam, npts=7, dims=3, evolve="rk4", q=4):
     """max over a theta grid of rho(G(theta)) for the isotropic unit-spaced
     problem with c tau / h = lam (h = 1, c = 1, dt = 2 lam).  ``dims`` = 1
     keeps theta2 = theta3 = 0 (a mode varying along x1 only)."""
     h = (1.0, 1.0, 1.0)
     dt = 2.0 * lam
-    blocks = hermite.corner_blocks(hermite.cell_matrix(m, h, 1.0, dt), m)
+    blocks = hermite.corner_blocks(hermite.cell_matrix(m, h, 1.0, dt, evolve, q), m)
     th = np.linspace(0.0, np.pi, npts)
     grid2 = th if dims == 3 else [0.0]
     rho = 0.0
@@ -46,11 +46,11 @@ def max_spectral_radius(m, lam, npts=7, dims=3):
     return rho
 
 
-def stability_limit(m, lo=0.05, hi=0.6, tol=1e-3, npts=7, dims=3):
+def stability_limit(m, lo=0.05, hi=0.6, tol=1e-3, npts=7, dims=3, evolve="rk4", q=4):
     """Largest lam = c tau / h (bisection to ``tol``) with max rho <= 1 + 1e-10."""
     while hi - lo > tol:
         mid = 0.5 * (lo + hi)
-        if max_spectral_radius(m, mid, npts, dims) <= 1.0 + 1e-10:
+        if max_spectral_radius(m, mid, npts, dims, evolve, q) <= 1.0 + 1e-10:
             lo = mid
         else:
             hi = mid

@@ -55,6 +55,8 @@ def _load():
         "hermite_destroy": (None, [P]),
         "hermite_step_dc": (I, [P, P, P, I, P]),
         "hermite_schedule_count": (I, [P]),
+        "hermite_set_taylor_order": (I, [P, I]),
+        "hermite_taylor_order": (I, [P]),
         "hermite_step_split_static": (I, [P, P, P, I, P]),
         "hermite_static_workspace_bytes": (S, []),
         "hermite_batch_plan": (I, [ctypes.POINTER(P), I, IP, IP, DP, DP, DP, I, I]),

@@ -146,12 +146,16 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     }
     const StepCoeffs<double> &cd = mode == kAdjoint ? p->adj : (mode == kDc ? p->dc : p->fwd);
     const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
+    const bool rk4 = p->q == 4;  // longer series run the kernels with more grades
     if (p->prec == HERMITE_FP64)
-      e = launch_fused_f64(p->m, p->tile, (const double *)in, (double *)out, g, cd, p->zchunk, st);
+      e = rk4 ? launch_fused_f64(p->m, p->tile, (const double *)in, (double *)out, g, cd, p->zchunk, st)
+              : launch_fused_f64_fullq(p->m, (const double *)in, (double *)out, g, cd, p->zchunk, st);
     else if (p->state == HERMITE_STATE_FP64)
-      e = launch_fused_f32_s64(p->m, p->tile, (const double *)in, (double *)out, g, cf, p->zchunk, st);
+      e = rk4 ? launch_fused_f32_s64(p->m, p->tile, (const double *)in, (double *)out, g, cf, p->zchunk, st)
+              : launch_fused_f32_fullq(p->m, kF64, in, out, g, cf, p->zchunk, st);
     else
-      e = launch_fused_f32_s32(p->m, p->tile, (const float *)in, (float *)out, g, cf, p->zchunk, st);
+      e = rk4 ? launch_fused_f32_s32(p->m, p->tile, (const float *)in, (float *)out, g, cf, p->zchunk, st)
+              : launch_fused_f32_fullq(p->m, kF32, in, out, g, cf, p->zchunk, st);
     if (e != cudaSuccess) return cuda_fail(e, "fused half-step launch");
     return HERMITE_OK;
   }
@@ -251,6 +255,29 @@ int host_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaStre
   return HERMITE_OK;
 }
 
+// (Re)build the forward, adjoint and dS/dc tables of the plan's q-stage
+// series, their FP32 copies and the double-float pairs of the hybrid modes.
+void build_tables(hermite_plan_s *p) {
+  const double tau = p->tau;
+  build_step_coeffs(p->m, p->h, p->c, tau, kForward, p->q, &p->fwd);
+  build_step_coeffs(p->m, p->h, p->c, tau, kAdjoint, p->q, &p->adj);
+  build_step_coeffs(p->m, p->h, p->c, tau, kDc, p->q, &p->dc);
+  p->fwd32 = cast_coeffs<float>(p->fwd);
+  p->adj32 = cast_coeffs<float>(p->adj);
+  p->dc32 = cast_coeffs<float>(p->dc);
+  const StepCoeffs<double> *srcs[3] = {&p->fwd, &p->adj, &p->dc};
+  HybridCoeffs *dsts[3] = {&p->hyb_fwd, &p->hyb_adj, &p->hyb_dc};
+  for (int k = 0; k < 3; ++k) {
+    dsts[k]->d = *srcs[k];
+    dsts[k]->hi = cast_coeffs<float>(*srcs[k]);
+    StepCoeffs<double> rest = *srcs[k];
+    double *r = &rest.gx[0][0];
+    const float *hi = &dsts[k]->hi.gx[0][0];
+    for (size_t q = 0; q < sizeof(StepCoeffs<double>) / sizeof(double); ++q) r[q] -= (double)hi[q];
+    dsts[k]->lo = cast_coeffs<float>(rest);
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -305,32 +332,31 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   p->variant = variant == HERMITE_AUTO ? HERMITE_FUSED : variant;
   p->elems = (size_t)2 * (m + 1) * (m + 1) * (m + 1) * nodes;
   build_H(m, p->H);
-  build_step_coeffs(m, h, c, tau, kForward, &p->fwd);
-  build_step_coeffs(m, h, c, tau, kAdjoint, &p->adj);
-  build_step_coeffs(m, h, c, tau, kDc, &p->dc);
-  p->fwd32 = cast_coeffs<float>(p->fwd);
-  p->adj32 = cast_coeffs<float>(p->adj);
-  p->dc32 = cast_coeffs<float>(p->dc);
-  const StepCoeffs<double> *srcs[3] = {&p->fwd, &p->adj, &p->dc};
-  HybridCoeffs *dsts[3] = {&p->hyb_fwd, &p->hyb_adj, &p->hyb_dc};
-  for (int k = 0; k < 3; ++k) {
-    dsts[k]->d = *srcs[k];
-    dsts[k]->hi = cast_coeffs<float>(*srcs[k]);
-    StepCoeffs<double> rest = *srcs[k];
-    double *r = &rest.gx[0][0];
-    const float *h = &dsts[k]->hi.gx[0][0];
-    for (size_t q = 0; q < sizeof(StepCoeffs<double>) / sizeof(double); ++q) r[q] -= (double)h[q];
-    dsts[k]->lo = cast_coeffs<float>(rest);
-  }
-  build_interp_coeffs(m, &p->interp);
+  build_tables(p);
   p->evolve.tau = tau;
   for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
+  p->evolve.q = 4;
+  build_interp_coeffs(m, &p->interp);
   p->tile = 0;
   p->zchunk = 16;
   p->ws_limit = (size_t)1 << 30;
   *out = p;
   return HERMITE_OK;
 }
+
+int hermite_set_taylor_order(hermite_plan_t p, int q) {
+  if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
+  if (q < 4 || q > 3 * (2 * p->m + 1))
+    return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * p->m + 1), p->m);
+  if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid precisions run the 4-stage series only");
+  p->q = q;
+  p->evolve.q = q;
+  build_tables(p);
+  return HERMITE_OK;
+}
+
+int hermite_taylor_order(hermite_plan_t p) { return p && !p->batch ? p->q : 0; }
 
 size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
 

@@ -190,7 +190,7 @@ int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *
     b->elems.push_back((size_t)2 * (m[i] + 1) * (m[i] + 1) * (m[i] + 1) * grid[3 * i] * grid[3 * i + 1] *
                        grid[3 * i + 2]);
     StepCoeffs<double> cd;
-    build_step_coeffs(m[i], h + 3 * i, c[i], 0.5 * dt[i], kForward, &cd);
+    build_step_coeffs(m[i], h + 3 * i, c[i], 0.5 * dt[i], kForward, 4, &cd);
     if (prec == HERMITE_FP64) {
       std::memcpy(host.data() + csize * i, &cd, csize);
     } else {

@@ -30,12 +30,15 @@
 
 namespace hermite {
 
-template <typename TC, int M, int TX, int TY>
+// G: largest total grade the kernel carries (2 for the 4-term series of RK4;
+// 2m for longer series, whose higher grades the z-pass tables fold in).
+template <typename TC, int M, int TX, int TY, int G = 2>
 struct FusedShape {
   static constexpr int NYN = TY + 1;
-  static constexpr int NA = (M == 2) ? 2 : 3;               // non-zero grades of G (G_2 = 0 for m = 1)
+  static constexpr int NA = (M - 1 < G ? M - 1 : G) + 1;   // grades a <= min(m, G) of the 1-D factors
+  static constexpr int NG = (2 * (NA - 1) < G ? 2 * (NA - 1) : G) + 1;  // grades of the y-pass results
   static constexpr int SX = 2 * M * M * NA * M * NYN * TX;  // x-pass results [f][iz][iy][a][ix'][ey][ex]
-  static constexpr int SY = 2 * 3 * M * M * M * TX * TY;    // y-pass results [f][g][iz][iy'][ix'][fy][fx]
+  static constexpr int SY = 2 * NG * M * M * M * TX * TY;   // y-pass results [f][g][iz][iy'][ix'][fy][fx]
   static constexpr size_t SMEM = (size_t)(SX + 2 * SY) * sizeof(TC);  // sY double-buffered by plane
   static constexpr int XITEMS = 2 * M * M * NYN * TX;       // (f, iz, iy, edge)
   static constexpr int YITEMS = 2 * M * M * TY * TX;        // (f, iz, ix', face)
@@ -52,12 +55,12 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // All NT threads of the CTA must call it; it starts and ends without a
 // pending barrier (callers that reuse sX, sY or `co` for another tile must
 // put a __syncthreads() between the calls).
-template <typename TS, typename TC, int M, int TX, int TY, int NT>
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
                                            TC *__restrict__ sX, TC *__restrict__ sY) {
-  using Sh = FusedShape<TC, M, TX, TY>;
-  constexpr int NYN = Sh::NYN, NA = Sh::NA;
+  using Sh = FusedShape<TC, M, TX, TY, G>;
+  constexpr int NYN = Sh::NYN, NA = Sh::NA, NG = Sh::NG;
   constexpr int XPT = (Sh::XITEMS + NT - 1) / NT;
   constexpr int YPT = (Sh::YITEMS + NT - 1) / NT;
   constexpr int ZPT = (Sh::ZITEMS + NT - 1) / NT;
@@ -97,7 +100,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     const int iz = t % M;
     const int f = t / M;
     ysrc[k] = ((f * M + iz) * M * NA * M + ixp) * XS + fy * TX + fx;
-    ydst[k] = e < Sh::YITEMS ? ((f * 3 * M + iz) * M * M + ixp) * YS + fy * TX + fx : -1;
+    ydst[k] = e < Sh::YITEMS ? ((f * NG * M + iz) * M * M + ixp) * YS + fy * TX + fx : -1;
   }
   // z-items: base in sY and the output node's in-plane offset (-1 if outside).
   int zsrc[ZPT], zxy[ZPT], zcomp[ZPT];
@@ -167,7 +170,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         }
       TC *yo = sY + (p & 1) * Sh::SY + ydst[k];
 #pragma unroll
-      for (int gg = 0; gg < 3; ++gg)
+      for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
         for (int r = 0; r < M; ++r) {
           TC acc = 0;
@@ -191,14 +194,14 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
 #pragma unroll
       for (int k = 0; k < ZPT; ++k) {
         if (zxy[k] < 0) continue;
-        TC sv[2][3][M], dv[2][3][M];
+        TC sv[2][NG][M], dv[2][NG][M];
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
-          for (int gg = 0; gg < 3; ++gg)
+          for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
             for (int iz = 0; iz < M; ++iz) {
-              const int q = zsrc[k] + ((f * 3 + gg) * M + iz) * M * M * YS;
+              const int q = zsrc[k] + ((f * NG + gg) * M + iz) * M * M * YS;
               const TC L = yp[q], R = yc[q];
               sv[f][gg][iz] = (iz & 1) ? R - L : R + L;
               dv[f][gg][iz] = (iz & 1) ? R + L : R - L;
@@ -212,7 +215,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
 #pragma unroll
             for (int fi = 0; fi < 2; ++fi)
 #pragma unroll
-              for (int gg = 0; gg < 3; ++gg)
+              for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
                 for (int i = 0; i < M; ++i)
                   acc = fma(co.kz[fo][fi][gg][r * 4 + i], (r & 1) ? dv[fi][gg][i] : sv[fi][gg][i], acc);
@@ -223,11 +226,11 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   }
 }
 
-template <typename TS, typename TC, int M, int TX, int TY, int NT>
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
 __global__ void __launch_bounds__(NT)
     fused_step_kernel(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
                       const StepCoeffs<TC> co) {
-  using Sh = FusedShape<TC, M, TX, TY>;
+  using Sh = FusedShape<TC, M, TX, TY, G>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC *sX = reinterpret_cast<TC *>(smem_raw);
   TC *sY = sX + Sh::SX;
@@ -236,14 +239,14 @@ __global__ void __launch_bounds__(NT)
   const int y0 = (blockIdx.x / tiles_x) * TY;
   const int z0 = g.zlo + blockIdx.y * zchunk;
   if (z0 >= g.zhi) return;
-  fused_tile<TS, TC, M, TX, TY, NT>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
+  fused_tile<TS, TC, M, TX, TY, NT, G>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
 }
 
-template <typename TS, typename TC, int M, int TX, int TY, int NT>
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
 cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoeffs<TC> &co,
                              int zchunk, cudaStream_t st) {
-  using Sh = FusedShape<TC, M, TX, TY>;
-  auto kern = fused_step_kernel<TS, TC, M, TX, TY, NT>;
+  using Sh = FusedShape<TC, M, TX, TY, G>;
+  auto kern = fused_step_kernel<TS, TC, M, TX, TY, NT, G>;
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);

@@ -9,4 +9,10 @@ cudaError_t launch_fused_f32_s32(int m, int tile, const float *in, float *out, c
   return dispatch_f32<float>(m, tile, in, out, g, co, zchunk, st);
 }
 
+cudaError_t launch_fused_f32_fullq(int m, int state, const void *in, void *out, const Geom &g,
+                                   const StepCoeffs<float> &co, int zchunk, cudaStream_t st) {
+  if (state == kF64) return launch_fused_f32_fullq_s64(m, (const double *)in, (double *)out, g, co, zchunk, st);
+  return dispatch_f32_fullq<float>(m, (const float *)in, (float *)out, g, co, zchunk, st);
+}
+
 }  // namespace hermite

@@ -25,4 +25,18 @@ cudaError_t dispatch_f32(int m, int tile, const TS *in, TS *out, const Geom &g, 
   return cudaErrorInvalidValue;
 }
 
+template <typename TS>
+cudaError_t dispatch_f32_fullq(int m, const TS *in, TS *out, const Geom &g, const StepCoeffs<float> &co,
+                               int zchunk, cudaStream_t st) {
+  switch (m) {  // grade bound G = 2m
+    case 1: return launch_fused_cfg<TS, float, 2, 16, 8, 512, 2>(in, out, g, co, zchunk, st);
+    case 2: return launch_fused_cfg<TS, float, 3, 8, 4, 288, 4>(in, out, g, co, zchunk, st);
+    case 3: return launch_fused_cfg<TS, float, 4, 4, 4, 256, 6>(in, out, g, co, zchunk, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_f32_fullq_s64(int m, const double *in, double *out, const Geom &g,
+                                       const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+
 }  // namespace hermite

@@ -9,4 +9,9 @@ cudaError_t launch_fused_f32_s64(int m, int tile, const double *in, double *out,
   return dispatch_f32<double>(m, tile, in, out, g, co, zchunk, st);
 }
 
+cudaError_t launch_fused_f32_fullq_s64(int m, const double *in, double *out, const Geom &g,
+                                       const StepCoeffs<float> &co, int zchunk, cudaStream_t st) {
+  return dispatch_f32_fullq<double>(m, in, out, g, co, zchunk, st);
+}
+
 }  // namespace hermite

@@ -28,4 +28,15 @@ cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, con
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_fused_f64_fullq(int m, const double *in, double *out, const Geom &g,
+                                   const StepCoeffs<double> &co, int zchunk, cudaStream_t st) {
+  using T = double;
+  switch (m) {  // grade bound G = 2m (m = 1 needs no more than the RK4 kernel)
+    case 1: return launch_fused_cfg<T, T, 2, 8, 8, 256, 2>(in, out, g, co, zchunk, st);
+    case 2: return launch_fused_cfg<T, T, 3, 4, 4, 160, 4>(in, out, g, co, zchunk, st);
+    case 3: return launch_fused_cfg<T, T, 4, 4, 2, 128, 6>(in, out, g, co, zchunk, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace hermite

@@ -18,11 +18,15 @@ constexpr int kMaxM = 4;  // largest M = m + 1
 // series of RK4 (Alg. 4).  Every G_a satisfies G[r][(left, i)] =
 // (-1)^(r+i) G[r][(right, i)], so only the right block is stored and the
 // kernels apply it to R_i + (-1)^(r+i) L_i (an even/odd butterfly).
+// Largest grade of the Kronecker factors in one dimension (a <= m <= 3) and
+// of the y-pass results (a + b <= 2m <= 6).
+constexpr int kMaxA = 4, kMaxG = 7;
+
 template <typename T>
 struct StepCoeffs {
-  T gx[3][16];        // right block of G_a along x1, [a][r * 4 + i]
-  T gy[3][16];        // same along x2
-  T kz[2][2][3][16];  // [f_out][f_in][grade g][r * 4 + i] = sum_c beta_{g+c} Gz_c (right block)
+  T gx[kMaxA][16];           // right block of G_a along x1, [a][r * 4 + i]
+  T gy[kMaxA][16];           // same along x2
+  T kz[2][2][kMaxG][16];     // [f_out][f_in][grade g][r * 4 + i] = sum_c beta_{g+c} Gz_c (right block)
 };
 
 // Tables of the split pair: the right block of H (interpolation) and the
@@ -34,6 +38,7 @@ struct InterpCoeffs {
 struct EvolveParams {
   double tau;     // half-step duration dt / 2
   double c2h[3];  // c^2 / h_k^2 along x1, x2, x3
+  int q;          // Taylor stages (Alg. 4)
 };
 
 // Host-side construction (exact rational arithmetic, then rounded once).
@@ -41,21 +46,22 @@ void build_H(int m, double *H);  // P x P row-major
 // mode: the half step S (kForward), its transpose S^T (kAdjoint), or its
 // derivative dS/dc with respect to the wave speed (kDc).
 enum CoeffMode { kForward = 0, kAdjoint = 1, kDc = 2 };
-void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
+// q: stages of the Taylor series of the local evolution (4 = RK4).
+void build_step_coeffs(int m, const double h[3], double c, double tau, int mode, int q,
                        StepCoeffs<double> *out);
 void build_interp_coeffs(int m, InterpCoeffs<double> *out);
 
 template <typename T>
 StepCoeffs<T> cast_coeffs(const StepCoeffs<double> &in) {
   StepCoeffs<T> o;
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < kMaxA; ++a)
     for (int k = 0; k < 16; ++k) {
       o.gx[a][k] = (T)in.gx[a][k];
       o.gy[a][k] = (T)in.gy[a][k];
     }
   for (int f = 0; f < 2; ++f)
     for (int g = 0; g < 2; ++g)
-      for (int s = 0; s < 3; ++s)
+      for (int s = 0; s < kMaxG; ++s)
         for (int k = 0; k < 16; ++k) o.kz[f][g][s][k] = (T)in.kz[f][g][s][k];
   return o;
 }
@@ -84,6 +90,12 @@ enum StateKind { kF64 = 0, kF32 = 1 };
 
 // Fused half step (forward or adjoint: the adjoint is the same kernel with
 // transposed tables and the mirrored offset).
+// Kernels for more than 4 Taylor stages (one tile shape each): enough grades
+// for any q <= 3(2m+1).
+cudaError_t launch_fused_f64_fullq(int m, const double *in, double *out, const Geom &g,
+                                   const StepCoeffs<double> &co, int zchunk, cudaStream_t st);
+cudaError_t launch_fused_f32_fullq(int m, int state, const void *in, void *out, const Geom &g,
+                                   const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
 // `tile` selects one of fused_tile_count(prec, m) compiled tile shapes.
 int fused_tile_count(int prec, int m);
 cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,

@@ -27,6 +27,7 @@ struct hermite_plan_s {
   hermite::HybridCoeffs hyb_fwd, hyb_adj, hyb_dc;
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
+  int q = 4;                // Taylor stages of the local evolution (4 = RK4)
   int tile;                 // fused kernel: index of the compiled tile shape
   int zchunk;               // fused kernel: cells per CTA along x3
   size_t ws_limit;          // split variant: workspace budget in bytes

@@ -1,8 +1,8 @@
 // Split pair of the half step (Sec. 3.1 + Sec. 3.2, the two-kernel design):
 //   interp_kernel  -- Alg. 2: Ru = (H (x) H (x) H) u_loc for every cell of a
 //                     z-slab, written to a workspace Ru[f][jz][jy][jx][cell];
-//   evolve_kernel  -- Alg. 4 with q = 4 (the Horner form of the Taylor series,
-//                     equal to classical RK4 for this linear operator) for the
+//   evolve_kernel  -- Alg. 4 with q stages (the Horner form of the Taylor
+//                     series; q = 4 equals classical RK4 here) for the
 //                     wave operator L(u, v) = (v, c^2 Delta u), Delta built
 //                     from Alg. 3 applied twice per dimension, then truncation
 //                     to the node data of the dual node (Sec. 2).
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NT)
 }
 
 // Evolution: CB cells per CTA, the coefficient tensors of each cell in shared
-// memory; w <- Ru + (tau/k) L w for k = 4..1 (Alg. 4), L w = (w_v, c^2 Delta w_u).
+// memory; w <- Ru + (tau/k) L w for k = q..1 (Alg. 4), L w = (w_v, c^2 Delta w_u).
 template <typename TS, typename TC, int M, int CB, int NT>
 __global__ void __launch_bounds__(NT)
     evolve_kernel(const TC *__restrict__ ru, TS *__restrict__ out, const Geom g, int zs0, int nzl,
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(NT)
   }
   __syncthreads();
   const TC c2h[3] = {(TC)ep.c2h[0], (TC)ep.c2h[1], (TC)ep.c2h[2]};
-  for (int k = 4; k >= 1; --k) {
+  for (int k = ep.q; k >= 1; --k) {
     const TC a = (TC)(ep.tau / k);
     for (int e = threadIdx.x; e < CB * P3; e += NT) {
       const int cb = e / P3, j = e - cb * P3;

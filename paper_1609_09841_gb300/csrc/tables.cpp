@@ -113,23 +113,26 @@ void build_interp_coeffs(int m, InterpCoeffs<double> *out) {
 // G_a[r][col] = (r+2a)!/r! H[r+2a][col] (zero when r + 2a > 2m+1): the
 // coefficients of order r <= m of d^{2a}/dxi^{2a} applied to the interpolant
 // (Alg. 3 twice per power of the Laplacian, then truncation of Sec. 2).
-void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
+void build_step_coeffs(int m, const double h[3], double c, double tau, int mode, int q,
                        StepCoeffs<double> *out) {
   const bool adjoint = mode == kAdjoint;
   const int M = m + 1, P = 2 * m + 2;
   Q Hq[8][8];
   exact_H(m, Hq);
-  double G[3][3][4][8];  // [dim][a][r][col], scaled by lam_k^(2a) / a!
+  // G_a = lam^(2a)/a! T1 (d^2/dxi^2)^a H for a <= m (higher powers vanish on
+  // degree 2m+1), per dimension.
+  double G[3][kMaxA][4][8];  // [dim][a][r][col]
   for (int k = 0; k < 3; ++k) {
     const double lam2 = (c * tau / h[k]) * (c * tau / h[k]);
-    for (int a = 0; a < 3; ++a) {
-      const double scale = (a == 0 ? 1.0 : (a == 1 ? lam2 : 0.5 * lam2 * lam2));
+    double scale = 1.0;  // lam2^a / a!
+    for (int a = 0; a < kMaxA; ++a) {
+      if (a > 0) scale *= lam2 / a;
       for (int r = 0; r < 4; ++r)
         for (int col = 0; col < 8; ++col) {
           double v = 0.0;
           if (r < M && col < P && r + 2 * a < P) {
             i128 fac = 1;
-            for (int q = r + 1; q <= r + 2 * a; ++q) fac *= q;
+            for (int qq = r + 1; qq <= r + 2 * a; ++qq) fac *= qq;
             v = (Q(fac) * Hq[r + 2 * a][col]).to_double() * scale;
           }
           G[k][a][r][col] = v;
@@ -137,27 +140,43 @@ void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
     }
   }
   // Right block (forward) or transposed left block (adjoint).
-  double GR[3][3][16];
+  double GR[3][kMaxA][16];
   for (int k = 0; k < 3; ++k)
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < kMaxA; ++a)
       for (int r = 0; r < 4; ++r)
         for (int i = 0; i < 4; ++i) {
           double v = 0.0;
           if (r < M && i < M) v = adjoint ? G[k][a][i][r] : G[k][a][r][M + i];
           GR[k][a][r * 4 + i] = v;
         }
-  // Field coupling of the 4-term Taylor series E = sum_q (tau L)^q / q!,
-  // L = [[0, I], [c^2 Delta, 0]], written per grade s of
-  // Lambda^s = s! sum_{a+b+c=s} prod_k (lam_k^2 d^2/dxi_k^2)^{a_k} / a_k!.
-  double beta[2][2][3];
-  const double uu[3] = {1.0, 0.5, 1.0 / 12.0};
-  const double uv[3] = {tau, tau / 6.0, 0.0};
-  const double vu[3] = {0.0, 1.0 / tau, 1.0 / (3.0 * tau)};
-  for (int s = 0; s < 3; ++s) {
-    beta[0][0][s] = uu[s];
-    beta[1][1][s] = uu[s];
-    beta[0][1][s] = adjoint ? vu[s] : uv[s];
-    beta[1][0][s] = adjoint ? uv[s] : vu[s];
+  // Field coupling of the q-term Taylor series E = sum_{k<=q} (tau L)^k / k!,
+  // L = [[0, I], [c^2 Delta, 0]], L^2 = c^2 Delta on both fields, written per
+  // grade s of Lambda^s = (tau^2 c^2 Delta)^s = s! sum_{a+b+c=s} prod_k
+  // (lam_k^2 d^2/dxi_k^2)^{a_k} / a_k!:
+  //   E_uu = E_vv = sum_{2s <= q} Lambda^s / (2s)!
+  //   E_uv = tau sum_{2s+1 <= q} Lambda^s / (2s+1)!
+  //   E_vu = tau^-1 sum_{1 <= s, 2s-1 <= q} Lambda^s / (2s-1)!
+  // so beta_s = s! times those coefficients.  (q = 4: uu = (1, 1/2, 1/12),
+  // uv = tau (1, 1/6), vu = (0, 1, 1/3) / tau.)
+  const int A = m < 3 ? m : 3;                 // largest grade per dimension
+  int S = (q + 1) / 2;                         // largest total grade with a non-zero beta
+  if (S > 3 * A) S = 3 * A;
+  double beta[2][2][3 * kMaxA];
+  for (int s = 0; s < 3 * kMaxA; ++s) {
+    double fs = 1.0;  // s!
+    for (int t = 2; t <= s; ++t) fs *= t;
+    auto inv_fact = [](int n) {
+      double v = 1.0;
+      for (int t = 2; t <= n; ++t) v /= t;
+      return v;
+    };
+    const double uu = (s <= S && 2 * s <= q) ? fs * inv_fact(2 * s) : 0.0;
+    const double uv = (s <= S && 2 * s + 1 <= q) ? tau * fs * inv_fact(2 * s + 1) : 0.0;
+    const double vu = (s >= 1 && s <= S && 2 * s - 1 <= q) ? fs * inv_fact(2 * s - 1) / tau : 0.0;
+    beta[0][0][s] = uu;
+    beta[1][1][s] = uu;
+    beta[0][1][s] = adjoint ? vu : uv;
+    beta[1][0][s] = adjoint ? uv : vu;
   }
   // Every term of grade s carries prod_k lam_k^(2 a_k), proportional to
   // c^(2s); beta does not depend on c.  Hence dS/dc is the same sum with
@@ -165,19 +184,22 @@ void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
   if (mode == kDc)
     for (int fo = 0; fo < 2; ++fo)
       for (int fi = 0; fi < 2; ++fi)
-        for (int s = 0; s < 3; ++s) beta[fo][fi][s] *= 2.0 * s / c;
-  for (int a = 0; a < 3; ++a)
-    for (int q = 0; q < 16; ++q) {
-      out->gx[a][q] = GR[0][a][q];
-      out->gy[a][q] = GR[1][a][q];
+        for (int s = 0; s < 3 * kMaxA; ++s) beta[fo][fi][s] *= 2.0 * s / c;
+  for (int a = 0; a < kMaxA; ++a)
+    for (int qq = 0; qq < 16; ++qq) {
+      out->gx[a][qq] = GR[0][a][qq];
+      out->gy[a][qq] = GR[1][a][qq];
     }
+  // y-pass results of grade g <= min(2A, S) exist; fold the z factors of
+  // grade c <= min(A, S - g) into Kz[g].
   for (int fo = 0; fo < 2; ++fo)
     for (int fi = 0; fi < 2; ++fi)
-      for (int g = 0; g < 3; ++g)
-        for (int q = 0; q < 16; ++q) {
+      for (int g = 0; g < kMaxG; ++g)
+        for (int qq = 0; qq < 16; ++qq) {
           double v = 0.0;
-          for (int cz = 0; cz + g <= 2; ++cz) v += beta[fo][fi][g + cz] * GR[2][cz][q];
-          out->kz[fo][fi][g][q] = v;
+          if (g <= 2 * A && g <= S)
+            for (int cz = 0; cz <= A && g + cz <= S; ++cz) v += beta[fo][fi][g + cz] * GR[2][cz][qq];
+          out->kz[fo][fi][g][qq] = v;
         }
 }
 

@@ -76,6 +76,14 @@ class Plan:
         import torch
         return torch.empty(self.shape, dtype=self.torch_dtype, device=device)
 
+    def set_taylor_order(self, q):
+        """Stages of the local Taylor evolution (4 = RK4, up to 3(2m+1))."""
+        capi.check(capi.lib.hermite_set_taylor_order(self.handle, int(q)))
+
+    @property
+    def taylor_order(self):
+        return capi.lib.hermite_taylor_order(self.handle)
+
     def schedule_count(self):
         return capi.lib.hermite_schedule_count(self.handle)
 

@@ -131,3 +131,19 @@ def test_batched_plan_rejected_by_single_calls_without_gpu(capi):
     assert capi.lib.hermite_batch_plan(ctypes.byref(p), 1, one, g, h, c, dt_bad, 1, 1) == -5
     assert capi.lib.hermite_batch_plan(ctypes.byref(p), 1, one, g, h, c, dt_bad, 0, 1) == -4
     assert not p.value
+
+
+def test_taylor_order_validation(capi):
+    rc, p = _plan(capi, m=2)
+    assert rc == 0
+    assert capi.lib.hermite_taylor_order(p) == 4
+    assert capi.lib.hermite_set_taylor_order(p, 3) == -1
+    assert capi.lib.hermite_set_taylor_order(p, 16) == -1          # 3(2m+1) = 15
+    assert capi.lib.hermite_set_taylor_order(p, 15) == 0
+    assert capi.lib.hermite_taylor_order(p) == 15
+    capi.lib.hermite_destroy(p)
+    rc, p = _plan(capi, m=2, prec=3, state=0)                        # double-float hybrid
+    assert rc == 0
+    assert capi.lib.hermite_set_taylor_order(p, 6) == -4
+    assert capi.lib.hermite_set_taylor_order(p, 4) == 0
+    capi.lib.hermite_destroy(p)

@@ -11,11 +11,12 @@ has degree <= 4 in t, so one RK4 (= Taylor q = 4) half step reproduces it
 exactly once its degree per variable is at most 2m+1.
 """
 from itertools import product
+from math import factorial
 
 import numpy as np
 import pytest
 
-from oracle import exact, hermite
+from oracle import exact, hermite, symbol
 
 
 def _lap(C):
@@ -110,3 +111,68 @@ def test_zero_and_constant_states(m):
     for p in (0, 1):
         out = hermite.half_step(S, m, h, 1.0, 0.05, p)
         assert np.max(np.abs(out - S)) <= 1e-13
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_full_taylor_equals_matrix_exponential(m):
+    """With q = d(2m+1) stages (Alg. 4's largest step, Sec. 3.2) the local
+    evolution is exact: L = [[0, I], [c^2 Delta, 0]] is nilpotent on the
+    polynomials of degree <= 2m+1 per variable (Delta lowers the total degree
+    by 2), so the q-term Taylor series equals exp(tau L), computed here by
+    scipy's Pade-based expm of the explicit matrix of L."""
+    from scipy.linalg import expm
+    P = 2 * m + 2
+    h, c, tau = (0.1, 0.13, 0.09), 1.1, 0.02
+    n = 2 * P ** 3
+    E = np.eye(n).reshape(n, 2, P, P, P)
+    Lu, Lv = hermite.wave_operator(E[:, 0], E[:, 1], c, h)
+    L = np.concatenate([Lu.reshape(n, -1), Lv.reshape(n, -1)], axis=1).T      # column k = L e_k
+    rng = np.random.default_rng(7)
+    B = rng.standard_normal((2, P, P, P))
+    q = 3 * (2 * m + 1)
+    wu, wv = hermite.evolve_taylor(B[0][None], B[1][None], tau, c, h, q=q)
+    ref = expm(tau * L) @ B.reshape(-1)
+    got = np.concatenate([wu.reshape(-1), wv.reshape(-1)])
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+    # and fewer stages are not exact
+    wu4, wv4 = hermite.evolve_taylor(B[0][None], B[1][None], tau, c, h, q=4)
+    assert np.max(np.abs(np.concatenate([wu4.reshape(-1), wv4.reshape(-1)]) - ref)) > 1e-8 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_polynomial_solution_full_taylor(m):
+    """Any polynomial solution of degree <= 2m+1 per variable is advanced
+    exactly by the full-order Taylor evolution (here p of total degree 2m+1
+    per the tensor space, with its exact time dependence from the series of
+    Delta^k p)."""
+    M, P = m + 1, 2 * m + 2
+    rng = np.random.default_rng(300 + m)
+    h = (0.11, 0.07, 0.09)
+    c = 1.3
+    tau = 0.2 * min(h) / c
+    xc = (0.05, -0.1, 0.2)
+    p = _random_poly(rng, P, max_total=3 * (2 * m + 1), max_each=2 * m + 1)
+    q0 = np.zeros_like(p)
+    # u(t) = sum_k t^(2k)/(2k)! c^(2k) Delta^k p,  v = u_t
+    u1, v1, D, k = np.zeros_like(p), np.zeros_like(p), p.copy(), 0
+    while np.any(D != 0):
+        u1 += tau ** (2 * k) / factorial(2 * k) * c ** (2 * k) * D
+        D = _lap(D)
+        k += 1
+        if np.any(D != 0):
+            v1 += tau ** (2 * k - 1) / factorial(2 * k - 1) * c ** (2 * k) * D
+    U = exact.poly_cell_data(m, p, q0, h, xc)
+    out = hermite.cell_map(U[None], m, h, c, tau, "taylor", q=3 * (2 * m + 1))[0]
+    for f, C in enumerate((u1, v1)):
+        ref = np.array([[[exact.poly_scaled_derivative(C, (i1, i2, i3), xc, h) for i1 in range(M)]
+                         for i2 in range(M)] for i3 in range(M)])
+        scale = max(1.0, np.max(np.abs(ref)), np.max(np.abs(U)))
+        assert np.max(np.abs(out[f] - ref)) <= {1: 1e-12, 2: 1e-11, 3: 1e-9}[m] * scale
+
+
+def test_full_taylor_is_stable_beyond_rk4_limit():
+    """Sec. 2: with the full series the step is limited only by the geometric
+    condition, so at m = 2 a half step with lam = 0.38 is stable for
+    q = 3(2m+1) and unstable for q = 4 (RK4)."""
+    assert symbol.max_spectral_radius(2, 0.38, npts=5, evolve="taylor", q=15) <= 1.0 + 1e-10
+    assert symbol.max_spectral_radius(2, 0.38, npts=5) > 1.0 + 1e-6
