@@ -59,9 +59,10 @@ def parse():
     ap.add_argument("--m", type=int, default=M_ORDER)
     ap.add_argument("--tile", type=int, default=-1, help="fixed schedule of the mixed leg (skips autotuning)")
     ap.add_argument("--zchunk", type=int, default=16)
-    ap.add_argument("--legs", default="mixed,mixed64,hybriddf,hybrid64,fp64,split,adjoint,batch,e2e",
+    ap.add_argument("--legs", default="mixed,mixed64,hybriddf,hybrid64,fp64,split,adjoint,taylor,batch,e2e",
                     help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), hybriddf, hybrid64, fp64, "
-                         "split (FP32 split pair), adjoint (FP32 adjoint step), batch (64 seeded simulations), e2e")
+                         "split (FP32 split pair), adjoint (FP32 adjoint step), taylor (full series vs RK4 at their "
+                         "stability limits), batch (64 seeded simulations), e2e")
     return ap.parse_args()
 
 
@@ -277,6 +278,20 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         ms_adj = e0.elapsed_time(e1) / args.steps
         extra["adjoint_fp32"] = {"value": world * dof / (max_over_ranks(ms_adj) * 1e-3), "ms_per_step": ms_adj}
+    if "taylor" in legs:        # full Taylor series (q = 3(2m+1)) vs RK4, each at its own stability limit
+        from paper_1609_09841_gb300 import stability_limit
+        q_full = 3 * (2 * m + 1)
+        legt = {}
+        for name, q in (("rk4", 4), ("full", q_full)):
+            lam = stability_limit(m, q)
+            dtq = 2.0 * lam * h[0]
+            planq = Plan(m, n, h, 1.0, dtq, prec="fp32", state="fp32", q=q)
+            msq = max_over_ranks(timed_steps(torch, planq, x, y, max(3, args.steps // 2), min(args.warmup, 3)))
+            legt[name] = {"q": q, "lam": lam, "ms_per_step": msq, "value": world * dof / (msq * 1e-3),
+                          "sim_time_per_s": 0.5 * dtq / (msq * 1e-3)}
+            del planq
+        legt["sim_time_gain_full_vs_rk4"] = legt["full"]["sim_time_per_s"] / legt["rk4"]["sim_time_per_s"]
+        extra["taylor_fp32"] = legt
     if "batch" in legs:         # 64 seeded simulations of uneven size and order, one persistent launch per half step
         extra["batch_fp32"] = run_batch(torch, rank)
     if "e2e" in legs:           # end to end through the C ABI with pinned host buffers (FP32 state)

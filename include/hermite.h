@@ -95,6 +95,15 @@ enum hermite_variant { HERMITE_AUTO = 0, HERMITE_FUSED = 1, HERMITE_SPLIT = 2 };
 int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c,
                  double dt, int prec, int state_dtype, int variant);
 
+/* The same with q Taylor stages for the local evolution (Alg. 4, Sec. 3.2;
+ * q = 4 is RK4 and hermite_plan is this call with q = 4).  q runs from 4 to
+ * 3(2m+1), where the series is exact for the cell polynomial.  The stability
+ * check is max_k c*(dt/2)/h_k <= hermite_stability_limit_taylor(m, q), so a
+ * plan with the full series may take a larger step than RK4 allows.  EINVAL
+ * for q outside 4..3(2m+1); EUNSUPPORTED for q != 4 with a hybrid precision. */
+int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c,
+                        double dt, int prec, int state_dtype, int variant, int q);
+
 /* One half step (Sec. 2): out = S_parity(in).  in and out are either both
  * device pointers (the step is only enqueued on `stream`) or both host
  * pointers (the library copies in -> device, steps and copies back through
@@ -214,13 +223,14 @@ int hermite_step_split_static(hermite_plan_t plan, const void *in_state, void *o
 /* HERMITE_STATIC_WORKSPACE_BYTES, as compiled into the library. */
 size_t hermite_static_workspace_bytes(void);
 
-/* Number of Taylor stages q of the local evolution (Alg. 4, Sec. 3.2).  The
- * default q = 4 is classical RK4 (the same polynomial in tau L).  Up to
+/* Change the number of Taylor stages q of the local evolution (Alg. 4,
+ * Sec. 3.2).  q = 4 is classical RK4 (the same polynomial in tau L).  Up to
  * q = 3(2m+1) = d(2N+1) stages the series is exact for the cell polynomial
- * (the paper's choice for the largest stable step; the library's stability
- * check stays the one of q = 4, which is the more restrictive).  Rebuilds the
- * plan's tables; the fused kernel then carries more grades of the series.
- * EINVAL outside 4..3(2m+1); EUNSUPPORTED for the hybrid precisions (4 only).
+ * (the paper's choice for the largest stable step).  Rebuilds the plan's
+ * tables; the fused kernel then carries more grades of the series.  EINVAL
+ * outside 4..3(2m+1); EUNSUPPORTED for the hybrid precisions (4 only);
+ * EUNSTABLE when the plan's c*(dt/2)/h exceeds
+ * hermite_stability_limit_taylor(m, q) (the plan keeps its old q).
  * Batched plans always use q = 4. */
 int hermite_set_taylor_order(hermite_plan_t plan, int q);
 int hermite_taylor_order(hermite_plan_t plan);
@@ -231,6 +241,11 @@ size_t hermite_state_elems(hermite_plan_t plan);
 /* Largest c*(dt/2)/h for which the half step of order m (1..3) is stable,
  * from the Fourier symbol of the isotropic half step; 0 for other m. */
 double hermite_stability_limit(int m);
+
+/* The same for q Taylor stages (4..3(2m+1)); 0 outside that range.  Not
+ * monotone in q: m = 3 with q = 5 is stable only up to 0.09, while the full
+ * series reaches 0.47 / 0.42 / 0.40 for m = 1 / 2 / 3. */
+double hermite_stability_limit_taylor(int m, int q);
 
 /* Copy the plan's 1-D interpolation operator H (P x P, row-major, H[j][(side,i)]:
  * monomial coefficient j from [left i = 0..m, right i = 0..m], Sec. 3.1) to

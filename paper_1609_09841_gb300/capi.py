@@ -46,11 +46,13 @@ def _load():
     IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     sig = {
         "hermite_plan": (I, [ctypes.POINTER(P), I, IP, DP, D, D, I, I, I]),
+        "hermite_plan_taylor": (I, [ctypes.POINTER(P), I, IP, DP, D, D, I, I, I, I]),
         "hermite_step": (I, [P, P, P, I, P]),
         "hermite_adjoint_step": (I, [P, P, P, I, P]),
         "hermite_error": (I, [P, P, P, U, DP, P]),
         "hermite_state_elems": (S, [P]),
         "hermite_stability_limit": (D, [I]),
+        "hermite_stability_limit_taylor": (D, [I, I]),
         "hermite_plan_operator": (I, [P, DP]),
         "hermite_destroy": (None, [P]),
         "hermite_step_dc": (I, [P, P, P, I, P]),

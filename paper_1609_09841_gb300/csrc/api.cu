@@ -40,10 +40,34 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 namespace {
 
-// Stability limit of c*tau/h per order, from the largest spectral radius of
-// the Fourier symbol of the isotropic half step over theta in [0, pi]^3
-// (bisection to 1e-3, rounded down).
-const double kStabilityLimit[4] = {0.0, 0.45, 0.30, 0.26};
+// Stability limit of c*tau/h per order m and Taylor order q, from the
+// largest spectral radius of the Fourier symbol of the isotropic half step
+// over a 7^3 grid of theta in [0, pi]^3 (bisection to 2e-4, rounded down to
+// two decimals).  q = 4 is RK4.  The limit is not monotone in q: the
+// truncated series of orders 5 and 6 damp or amplify the highest modes
+// differently, and m = 3 with q = 5 is stable only up to 0.09.
+constexpr int kMaxQ = 21;
+const double kStabilityLimit[4][kMaxQ + 1] = {
+    {0},
+    {0, 0, 0, 0, 0.45, 0.47, 0.47, 0.47, 0.47, 0.47},
+    {0, 0, 0, 0, 0.30, 0.34, 0.38, 0.36, 0.41, 0.42, 0.42, 0.42, 0.42, 0.42, 0.42, 0.42},
+    {0, 0, 0, 0, 0.26, 0.09, 0.20, 0.24, 0.33, 0.40, 0.40, 0.40, 0.40, 0.40, 0.40, 0.40, 0.40, 0.40, 0.40,
+     0.40, 0.40, 0.40},
+};
+
+double limit_of(int m, int q) {
+  return (m >= 1 && m <= 3 && q >= 4 && q <= 3 * (2 * m + 1)) ? kStabilityLimit[m][q] : 0.0;
+}
+
+int check_stable(int m, int q, double c, double tau, const double h[3]) {
+  for (int k = 0; k < 3; ++k) {
+    const double lam = c * tau / h[k];
+    if (lam > limit_of(m, q) * (1.0 + 1e-12))
+      return fail(HERMITE_EUNSTABLE, "c*(dt/2)/h[%d] = %.6g above the stability limit %.3g of order %d, q = %d", k,
+                  lam, limit_of(m, q), m, q);
+  }
+  return HERMITE_OK;
+}
 
 size_t state_bytes(const hermite_plan_s *p) {
   return p->elems * (p->state == HERMITE_STATE_FP64 ? sizeof(double) : sizeof(float));
@@ -284,10 +308,17 @@ extern "C" {
 
 const char *hermite_last_error(void) { return g_last_error.c_str(); }
 
-double hermite_stability_limit(int m) { return (m >= 1 && m <= 3) ? kStabilityLimit[m] : 0.0; }
+double hermite_stability_limit(int m) { return limit_of(m, 4); }
+
+double hermite_stability_limit_taylor(int m, int q) { return limit_of(m, q); }
 
 int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c, double dt,
                  int prec, int state_dtype, int variant) {
+  return hermite_plan_taylor(out, m, grid, h, c, dt, prec, state_dtype, variant, 4);
+}
+
+int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c, double dt,
+                        int prec, int state_dtype, int variant, int q) {
   g_last_error.clear();
   if (!out) return fail(HERMITE_EINVAL, "out is NULL");
   *out = nullptr;
@@ -309,13 +340,12 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
     return fail(HERMITE_EINVAL, "variant %d unknown", variant);
   if (variant == HERMITE_SPLIT && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
     return fail(HERMITE_EUNSUPPORTED, "the split variant has no hybrid precision");
+  if (q < 4 || q > 3 * (2 * m + 1))
+    return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * m + 1), m);
+  if (q != 4 && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid precisions run the 4-stage series only");
   const double tau = 0.5 * dt;
-  for (int k = 0; k < 3; ++k) {
-    const double lam = c * tau / h[k];
-    if (lam > kStabilityLimit[m] * (1.0 + 1e-12))
-      return fail(HERMITE_EUNSTABLE, "c*(dt/2)/h[%d] = %.6g above the stability limit %.3g of order %d", k, lam,
-                  kStabilityLimit[m], m);
-  }
+  if (int rc = check_stable(m, q, c, tau, h)) return rc;
   const size_t nodes = (size_t)grid[0] * grid[1] * grid[2];
   hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
   if (!p) return fail(HERMITE_ENOMEM, "plan allocation");
@@ -328,6 +358,7 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   p->dt = dt;
   p->tau = tau;
   p->prec = prec;
+  p->q = q;
   p->state = state_dtype;
   p->variant = variant == HERMITE_AUTO ? HERMITE_FUSED : variant;
   p->elems = (size_t)2 * (m + 1) * (m + 1) * (m + 1) * nodes;
@@ -335,7 +366,7 @@ int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3
   build_tables(p);
   p->evolve.tau = tau;
   for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
-  p->evolve.q = 4;
+  p->evolve.q = q;
   build_interp_coeffs(m, &p->interp);
   p->tile = 0;
   p->zchunk = 16;
@@ -350,6 +381,7 @@ int hermite_set_taylor_order(hermite_plan_t p, int q) {
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * p->m + 1), p->m);
   if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF))
     return fail(HERMITE_EUNSUPPORTED, "the hybrid precisions run the 4-stage series only");
+  if (int rc = check_stable(p->m, q, p->c, p->tau, p->h)) return rc;
   p->q = q;
   p->evolve.q = q;
   build_tables(p);

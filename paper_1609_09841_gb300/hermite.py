@@ -16,9 +16,10 @@ STATES = {"fp64": capi.HERMITE_STATE_FP64, "fp32": capi.HERMITE_STATE_FP32}
 VARIANTS = {"auto": capi.HERMITE_AUTO, "fused": capi.HERMITE_FUSED, "split": capi.HERMITE_SPLIT}
 
 
-def stability_limit(m):
-    """Largest c*(dt/2)/h with a stable half step of order m."""
-    return capi.lib.hermite_stability_limit(int(m))
+def stability_limit(m, q=4):
+    """Largest c*(dt/2)/h with a stable half step of order m and q Taylor
+    stages (q = 4 is RK4)."""
+    return capi.lib.hermite_stability_limit_taylor(int(m), int(q))
 
 
 def _ptr(x):
@@ -41,15 +42,16 @@ def _stream(stream):
 
 class Plan:
     """A half-step plan: order m, periodic grid (n1, n2, n3), spacings h, wave
-    speed c and FULL time step dt (each step advances dt / 2)."""
+    speed c and FULL time step dt (each step advances dt / 2); q Taylor stages
+    of the local evolution (4 = RK4, up to 3(2m+1))."""
 
-    def __init__(self, m, grid, h, c, dt, prec="fp64", state="fp64", variant="auto"):
+    def __init__(self, m, grid, h, c, dt, prec="fp64", state="fp64", variant="auto", q=4):
         self.m, self.grid, self.h = int(m), tuple(int(v) for v in grid), tuple(float(v) for v in h)
         self.c, self.dt, self.prec, self.state, self.variant = float(c), float(dt), prec, state, variant
         handle = ctypes.c_void_p()
-        capi.check(capi.lib.hermite_plan(ctypes.byref(handle), self.m, (ctypes.c_int * 3)(*self.grid),
-                                         (ctypes.c_double * 3)(*self.h), self.c, self.dt,
-                                         PRECISIONS[prec], STATES[state], VARIANTS[variant]))
+        capi.check(capi.lib.hermite_plan_taylor(ctypes.byref(handle), self.m, (ctypes.c_int * 3)(*self.grid),
+                                                (ctypes.c_double * 3)(*self.h), self.c, self.dt,
+                                                PRECISIONS[prec], STATES[state], VARIANTS[variant], int(q)))
         self._h = handle
 
     @property

@@ -147,3 +147,50 @@ def test_taylor_order_validation(capi):
     assert capi.lib.hermite_set_taylor_order(p, 6) == -4
     assert capi.lib.hermite_set_taylor_order(p, 4) == 0
     capi.lib.hermite_destroy(p)
+
+
+Q_TABLE_CASES = [(1, q) for q in range(4, 10)] + [(2, q) for q in range(4, 16)] + [(3, 5), (3, 6), (3, 21)]
+
+
+@pytest.mark.parametrize("m,q", Q_TABLE_CASES)
+def test_taylor_stability_table_agrees_with_symbol(capi, m, q):
+    """Each entry of the per-q table is stable by the oracle's symbol of the
+    q-stage Taylor half step and 0.02 above it is not (entries are rounded
+    down to two decimals, so 0.02 above is past the true limit)."""
+    lim = capi.lib.hermite_stability_limit_taylor(m, q)
+    assert lim > 0
+    assert symbol.max_spectral_radius(m, lim, npts=7, evolve="taylor", q=q) <= 1.0 + 1e-10
+    assert symbol.max_spectral_radius(m, lim + 0.02, npts=7, evolve="taylor", q=q) > 1.0 + 1e-9
+
+
+def _plan_q(capi, m, q, dt, grid=(16, 16, 16), prec=0):
+    h = tuple(1.0 / g for g in grid)
+    p = ctypes.c_void_p()
+    rc = capi.lib.hermite_plan_taylor(ctypes.byref(p), m, (ctypes.c_int * 3)(*grid), (ctypes.c_double * 3)(*h),
+                                      1.0, dt, prec, 0, 0, q)
+    return rc, p
+
+
+def test_plan_taylor_checks_its_own_limit(capi):
+    """A full-series plan accepts a step RK4 rejects; a lower q that is less
+    stable rejects a step RK4 accepts; set_taylor_order checks the same."""
+    h = 1.0 / 16
+    assert capi.lib.hermite_stability_limit_taylor(2, 3) == 0.0
+    assert capi.lib.hermite_stability_limit_taylor(2, 16) == 0.0
+    assert capi.lib.hermite_stability_limit_taylor(2, 4) == capi.lib.hermite_stability_limit(2)
+    big = 2 * 0.40 * h                      # lam = 0.40: above RK4's 0.30, below the full series' 0.42
+    assert _plan_q(capi, 2, 4, big)[0] == -5
+    rc, p = _plan_q(capi, 2, 15, big)
+    assert rc == 0 and capi.lib.hermite_taylor_order(p) == 15
+    assert capi.lib.hermite_set_taylor_order(p, 4) == -5    # would be unstable: refused, q kept
+    assert capi.lib.hermite_taylor_order(p) == 15
+    capi.lib.hermite_destroy(p)
+    mid = 2 * 0.15 * h                      # lam = 0.15: fine for RK4 (0.26), not for m = 3, q = 5 (0.09)
+    assert _plan_q(capi, 3, 5, mid)[0] == -5
+    rc, p = _plan_q(capi, 3, 4, mid)
+    assert rc == 0
+    assert capi.lib.hermite_set_taylor_order(p, 5) == -5
+    assert capi.lib.hermite_set_taylor_order(p, 21) == 0
+    capi.lib.hermite_destroy(p)
+    assert _plan_q(capi, 2, 6, 2 * 0.2 * h, prec=2)[0] == -4   # hybrid: q = 4 only
+    assert _plan_q(capi, 2, 2, 2 * 0.2 * h)[0] == -1

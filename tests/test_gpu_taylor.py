@@ -72,3 +72,29 @@ def test_taylor_q_fp32(torch_cuda, m, q, state):
         ref = oracle.half_step(x, m, h, 1.0, dt, parity, evolve="taylor", q=q)
         assert _relmax(yd.double().cpu().numpy(), ref) <= 2e-5, parity
 
+
+
+def test_full_series_runs_at_a_step_rk4_cannot_take(torch_cuda):
+    """m = 2, q = 15 at lam = 0.41 (RK4's limit is 0.30): the first half steps
+    match the oracle's q = 15 run and 200 half steps stay bounded."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import Plan, stability_limit
+    m, q, n = 2, 15, (12, 12, 12)
+    h = (1.0 / 12,) * 3
+    lam = 0.41
+    assert stability_limit(m, 4) < lam <= stability_limit(m, q)
+    dt = 2 * lam * h[0]
+    plan = Plan(m, n, h, 1.0, dt, q=q)
+    x = HI.random_state(m, n, seed=7)
+    ref = oracle.run(x, m, h, 1.0, dt, 4, evolve="taylor", q=q)
+    a = torch.from_numpy(x).cuda()
+    b = torch.empty_like(a)
+    for k in range(4):
+        plan.step(a, b, k % 2)
+        a, b = b, a
+    assert _relmax(a.cpu().numpy(), ref) <= 1e-12
+    amp0 = float(a.abs().max())
+    for k in range(196):
+        plan.step(a, b, k % 2)
+        a, b = b, a
+    assert torch.isfinite(a).all() and float(a.abs().max()) <= 2.0 * amp0
