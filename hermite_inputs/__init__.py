@@ -14,7 +14,8 @@ from math import factorial, pi
 import numpy as np
 
 __all__ = ["random_state", "gaussian_pulse", "standing_modes", "standing_mode_draw",
-           "product_standing_mode", "batch_draw", "receiver_draw", "state_shape"]
+           "product_standing_mode", "batch_draw", "receiver_draw", "state_shape",
+           "advection_random_state", "plane_wave"]
 
 
 def state_shape(m, n):
@@ -124,3 +125,31 @@ def receiver_draw(seed, n, count=32):
     """Seeded distinct receiver node indices (flat index z*n2*n1 + y*n1 + x)."""
     rng = np.random.default_rng(seed)
     return np.sort(rng.choice(n[0] * n[1] * n[2], size=count, replace=False)).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Advection (Eq. 1): one field, layout A[i3, i2, i1, z, y, x].
+# ---------------------------------------------------------------------------
+
+
+def advection_random_state(m, n, seed, decay=0.5):
+    """Seeded one-field state: the u field of ``random_state``."""
+    return random_state(m, n, seed, decay)[0].copy()
+
+
+def plane_wave(m, n, h, k=(1, 1, 1), phase=0.0, grid=0):
+    """u = sin(2 pi k . x + phase) as one-field node data on the primal
+    (grid 0) or dual (grid 1) grid.  Its scaled derivative of order i is
+    prod_d (2 pi k_d h_d)^{i_d} / i_d! * sin(2 pi k . x + phase + |i| pi / 2)."""
+    M = m + 1
+    X = [_coords(n[d], h[d], grid) for d in range(3)]
+    z, y, x = np.meshgrid(X[2], X[1], X[0], indexing="ij")
+    arg = 2 * pi * (k[0] * x + k[1] * y + k[2] * z) + phase
+    A = np.empty((M, M, M, n[2], n[1], n[0]))
+    for i3 in range(M):
+        for i2 in range(M):
+            for i1 in range(M):
+                w = ((2 * pi * k[0] * h[0]) ** i1 / factorial(i1) * (2 * pi * k[1] * h[1]) ** i2 / factorial(i2)
+                     * (2 * pi * k[2] * h[2]) ** i3 / factorial(i3))
+                A[i3, i2, i1] = w * np.sin(arg + (i1 + i2 + i3) * pi / 2)
+    return A

@@ -89,16 +89,18 @@ def _offset(parity):
 def gather_cells(S, m, parity, z_cells=None):
     """Local tensors u_loc of every target cell in an output z-range.
 
-    Returns U of shape (ncell, 2, P, P, P) indexed [cell, f, tz, ty, tx] with
+    Returns U of shape (ncell, F, P, P, P) indexed [cell, f, tz, ty, tx] with
     t = side * M + i along each dimension (side 0 = lower corner, 1 = upper),
-    cells ordered (z, y, x) with x fastest, z in ``z_cells``.
+    cells ordered (z, y, x) with x fastest, z in ``z_cells``; F = S.shape[0]
+    fields (2 for the wave equation, 1 for advection).
     """
     M, P = m + 1, 2 * m + 2
+    F = S.shape[0]
     nz, ny, nx = S.shape[-3:]
     s = _offset(parity)
     zs = np.arange(nz) if z_cells is None else np.asarray(z_cells)
     ys, xs = np.arange(ny), np.arange(nx)
-    U = np.empty((len(zs), ny, nx, 2, P, P, P))
+    U = np.empty((len(zs), ny, nx, F, P, P, P))
     for c in (0, 1):
         zi = (zs + s + c) % nz
         for b in (0, 1):
@@ -108,7 +110,7 @@ def gather_cells(S, m, parity, z_cells=None):
                 blk = S[:, :, :, :][..., zi, :, :][..., yi, :][..., xi]  # (2,M,M,M,cz,ny,nx)
                 U[:, :, :, :, c * M:(c + 1) * M, b * M:(b + 1) * M, a * M:(a + 1) * M] = \
                     blk.transpose(4, 5, 6, 0, 1, 2, 3)
-    return U.reshape(len(zs) * ny * nx, 2, P, P, P)
+    return U.reshape(len(zs) * ny * nx, F, P, P, P)
 
 
 # ---------------------------------------------------------------------------
