@@ -59,10 +59,11 @@ def parse():
     ap.add_argument("--m", type=int, default=M_ORDER)
     ap.add_argument("--tile", type=int, default=-1, help="fixed schedule of the mixed leg (skips autotuning)")
     ap.add_argument("--zchunk", type=int, default=16)
-    ap.add_argument("--legs", default="mixed,mixed64,hybriddf,hybrid64,fp64,split,adjoint,taylor,batch,e2e",
+    ap.add_argument("--legs", default="mixed,mixed64,hybriddf,hybrid64,fp64,split,adjoint,taylor,advection,batch,e2e",
                     help="comma list of mixed (FP32/FP32), mixed64 (FP32/FP64 state), hybriddf, hybrid64, fp64, "
                          "split (FP32 split pair), adjoint (FP32 adjoint step), taylor (full series vs RK4 at their "
-                         "stability limits), batch (64 seeded simulations), e2e")
+                         "stability limits), advection (Table 1: 150^3, 200 time steps, m = 1..3), "
+                         "batch (64 seeded simulations), e2e")
     return ap.parse_args()
 
 
@@ -294,6 +295,8 @@ def run_ours(args, rank, world):
             del planq
         legt["sim_time_gain_full_vs_rk4"] = legt["full"]["sim_time_per_s"] / legt["rk4"]["sim_time_per_s"]
         extra["taylor_fp32"] = legt
+    if "advection" in legs:     # the paper's own workload (Table 1): advection, 150^3, 200 time steps
+        extra["advection_table1"] = run_advection(torch, rank, world, max_over_ranks, hbm_peak)
     if "batch" in legs:         # 64 seeded simulations of uneven size and order, one persistent launch per half step
         extra["batch_fp32"] = run_batch(torch, rank)
     if "e2e" in legs:           # end to end through the C ABI with pinned host buffers (FP32 state)
@@ -357,6 +360,60 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline()
     if dist is not None:
         dist.destroy_process_group()
+    return out
+
+
+# Table 1 of the paper: advection on a 150^3 grid, 200 time steps (400 half
+# steps), GTX 980, FP32; the number of stages is not stated there.
+TABLE1_SECONDS = {1: {"monolithic": 2.09, "two_kernels": 2.42}, 2: {"monolithic": 13.77, "two_kernels": 13.77},
+                  3: {"monolithic": 36.17, "two_kernels": 37.23}}
+
+
+def run_advection(torch, rank, world, max_over_ranks, hbm_peak, side=150, nsteps=200):
+    """Time to solution of Table 1's workload: u_t = u_x1 + u_x2 + u_x3 on a
+    periodic side^3 grid, seeded N(0,1) state, FP32, the whole Taylor series
+    (q = 3(2m+1)), dt = 0.9 h (a tau / h = 0.45), nsteps full steps = 2 nsteps
+    half steps, fused Kronecker kernel and split pair (interpolation kernel +
+    Alg. 4 loop).  Inputs 0.1-0.9 GB (> L2 from m = 2 on)."""
+    from paper_1609_09841_gb300 import AdvectionPlan
+    import hermite_inputs as HI
+    out = {"workload": f"advection u_t = u_x1 + u_x2 + u_x3, {side}^3 periodic, {nsteps} time steps "
+                       f"({2 * nsteps} half steps), FP32, q = 3(2m+1), dt = 0.9 h",
+           "paper_gtx980_seconds": TABLE1_SECONDS}
+    h = (1.0 / side,) * 3
+    for m in (1, 2, 3):
+        x0 = torch.from_numpy(HI.advection_random_state(m, (side,) * 3, seed=150 + m + 7 * rank,
+                                                        dtype=np.float32)).cuda()
+        row = {}
+        for variant in ("fused", "split"):
+            plan = AdvectionPlan(m, (side,) * 3, h, (1.0, 1.0, 1.0), 0.9 * h[0], prec="fp32", state="fp32",
+                                 variant=variant)
+            a, b = x0.clone(), torch.empty_like(x0)
+            for k in range(4):
+                plan.step(a, b, k % 2)
+                a, b = b, a
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.copy_(x0)
+            e0.record()
+            for k in range(2 * nsteps):
+                plan.step(a, b, k % 2)
+                a, b = b, a
+            e1.record()
+            torch.cuda.synchronize()
+            sec = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
+            half_ms = sec * 1e3 / (2 * nsteps)
+            dof = (m + 1) ** 3 * side ** 3
+            bytes_alg = 2 * dof * 4
+            row[variant] = {"seconds_to_solution": sec, "ms_per_half_step": half_ms,
+                            "value": world * dof / (half_ms * 1e-3), "unit": "DOF-updates/s",
+                            "hbm_gbs_algorithmic": bytes_alg / (half_ms * 1e-3) / 1e9,
+                            "hbm_frac": bytes_alg / (half_ms * 1e-3) / 1e9 / hbm_peak}
+            del plan
+        key = {"fused": "monolithic", "split": "two_kernels"}
+        row["speedup_vs_paper"] = {v: TABLE1_SECONDS[m][key[v]] / row[v]["seconds_to_solution"] for v in key}
+        out[f"m={m}"] = row
+        del x0
     return out
 
 

@@ -132,9 +132,16 @@ def receiver_draw(seed, n, count=32):
 # ---------------------------------------------------------------------------
 
 
-def advection_random_state(m, n, seed, decay=0.5):
-    """Seeded one-field state: the u field of ``random_state``."""
-    return random_state(m, n, seed, decay)[0].copy()
+def advection_random_state(m, n, seed, decay=0.5, dtype=np.float64):
+    """Seeded one-field N(0, 1) state (shape (M, M, M, n3, n2, n1)), component
+    i scaled by decay^|i| as in ``random_state``; drawn directly in ``dtype``."""
+    rng = np.random.default_rng(seed)
+    M = m + 1
+    A = rng.standard_normal((M, M, M, n[2], n[1], n[0]), dtype=dtype)
+    i = np.arange(M)
+    w = (decay ** (i[:, None, None] + i[None, :, None] + i[None, None, :])).astype(dtype)
+    A *= w[:, :, :, None, None, None]
+    return A
 
 
 def plane_wave(m, n, h, k=(1, 1, 1), phase=0.0, grid=0):

@@ -235,7 +235,40 @@ size_t hermite_static_workspace_bytes(void);
 int hermite_set_taylor_order(hermite_plan_t plan, int q);
 int hermite_taylor_order(hermite_plan_t plan);
 
-/* Number of state elements: 2 * (m+1)^3 * n1*n2*n3. */
+/* ---- Advection (Eq. 1) -------------------------------------------------
+ * The 3-D advection equation of Sec. 2 with a constant velocity a:
+ *   u_t = a1 u_x1 + a2 u_x2 + a3 u_x3   (Eq. 1 is a = (1, 1, 1)),
+ * whose exact solution is u(x, t) = u(x + a t, 0).  One field: the state is
+ * u[i3][i2][i1][n3][n2][n1] with the scaling and staggering of the wave
+ * equation's states, (m+1)^3 * n1*n2*n3 elements.  The half step interpolates
+ * (Sec. 3.1), evolves with the q-stage Hermite-Taylor loop (Alg. 4, the
+ * recursion of Eq. 5) over dt/2 and truncates to orders <= m (Sec. 2).
+ *
+ * q = 0 selects q = 3(2m+1) = d(2N+1), the whole series, for which the
+ * evolution is the exact translation of the cell polynomial and the half step
+ * is one Kronecker product of 1-D maps (FUSED kernel).  1 <= q < 3(2m+1) runs
+ * the SPLIT pair (interpolation kernel, then the Alg. 4 loop); AUTO picks
+ * FUSED for the whole series and SPLIT otherwise; FUSED with a shorter series
+ * is EUNSUPPORTED.  prec: FP64 (FP64 state) or FP32 (FP32 or FP64 state);
+ * the hybrid precisions are EUNSUPPORTED.  The plan checks
+ * max_k |a_k| (dt/2)/h_k <= hermite_adv_stability_limit(m, q) (EUNSTABLE).
+ *
+ * hermite_step, hermite_error (mask bit 1 only; bit 2 selects a field that
+ * does not exist: EINVAL), hermite_dot, hermite_state_elems,
+ * hermite_set_schedule (tile 0, zchunk), hermite_plan_operator and
+ * hermite_destroy take advection plans; the adjoint, dS/dc, receiver,
+ * Taylor-order, batched and allocation-free calls return EUNSUPPORTED. */
+int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], const double a[3],
+                     double dt, int q, int prec, int state_dtype, int variant);
+
+/* Largest max_k |a_k| (dt/2)/h_k of a stable advection half step of order m
+ * with q stages (0: the whole series, whose limit is the half cell of Sec. 2,
+ * 0.5).  The smaller of the Fourier-symbol limits for a mode along x1 and for
+ * the diagonal direction, rounded down to two decimals; 0 where no step is
+ * stable (q = 1) or for arguments out of range. */
+double hermite_adv_stability_limit(int m, int q);
+
+/* Number of state elements: 2 * (m+1)^3 * n1*n2*n3 (advection: (m+1)^3 * n1*n2*n3). */
 size_t hermite_state_elems(hermite_plan_t plan);
 
 /* Largest c*(dt/2)/h for which the half step of order m (1..3) is stable,

@@ -101,16 +101,18 @@ def cell_map(U, m, h, a, tau, q=None):
     return R[:, :M, :M, :M]
 
 
-def half_step(A, m, h, a, dt, parity, q=None, chunk_cells=8192):
-    """One half step of the whole grid; A has shape (M, M, M, nz, ny, nx)."""
+def half_step(A, m, h, a, dt, parity, q=None, z_cells=None, chunk_cells=8192):
+    """One half step of the whole grid; A has shape (M, M, M, nz, ny, nx).
+    ``z_cells`` restricts the output to those z layers (the rest is NaN)."""
     A = np.asarray(A, dtype=np.float64)
     M = m + 1
     assert A.shape[:3] == (M, M, M), A.shape
     nz, ny, nx = A.shape[-3:]
-    out = np.empty_like(A)
+    out = np.full_like(A, np.nan)
+    zs = np.arange(nz) if z_cells is None else np.asarray(z_cells)
     per = max(1, chunk_cells // (ny * nx))
-    for z0 in range(0, nz, per):
-        zc = np.arange(z0, min(nz, z0 + per))
+    for k in range(0, len(zs), per):
+        zc = zs[k:k + per]
         U = hermite.gather_cells(A[None], m, parity, zc)[:, 0]
         V = cell_map(U, m, h, a, 0.5 * dt, q)
         out[..., zc, :, :] = V.reshape(len(zc), ny, nx, M, M, M).transpose(3, 4, 5, 0, 1, 2)

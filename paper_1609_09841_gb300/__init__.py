@@ -2,4 +2,4 @@
 
 ``Plan`` wraps the C ABI of libhermite (include/hermite.h); the arithmetic
 runs only in that CUDA library, which must be built (``build.build()``)."""
-from .hermite import Plan, stability_limit  # noqa: F401
+from .hermite import AdvectionPlan, Plan, adv_stability_limit, stability_limit  # noqa: F401

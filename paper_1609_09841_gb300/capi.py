@@ -53,6 +53,8 @@ def _load():
         "hermite_state_elems": (S, [P]),
         "hermite_stability_limit": (D, [I]),
         "hermite_stability_limit_taylor": (D, [I, I]),
+        "hermite_adv_plan": (I, [ctypes.POINTER(P), I, IP, DP, DP, D, I, I, I, I]),
+        "hermite_adv_stability_limit": (D, [I, I]),
         "hermite_plan_operator": (I, [P, DP]),
         "hermite_destroy": (None, [P]),
         "hermite_step_dc": (I, [P, P, P, I, P]),

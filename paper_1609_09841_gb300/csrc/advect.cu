@@ -1,0 +1,337 @@
+// Advection half step kernels (Eq. 1 with a constant velocity; Sec. 2,
+// Sec. 3.1, Alg. 4).  See advect.h for the factorisation.
+//
+// adv_kron_kernel applies a Kronecker product Gz (x) Gy (x) Gx of R x P
+// factors to the 2 x 2 x 2 corner data of every cell:
+//   * a CTA owns TX x TY cells in (x1, x2) and walks `zchunk` cells along x3,
+//     streaming node layers: each layer of nodes is read from HBM once;
+//   * x-pass, per (x1-edge, node row, i3, i2): R outputs from the P values of
+//     the two x1-neighbours (coalesced along x1), into shared memory;
+//   * y-pass, per (cell column, i3, r1): R outputs from the two node rows,
+//     into one of two layer buffers;
+//   * z-pass, per (cell, r2, r1): R outputs from the two layer buffers, to
+//     the output state (R = M, fused half step) or to the split workspace
+//     (R = P, interpolation only).
+// Every periodic index is wrapped once: a cell index c < n gives node
+// indices c + s + side in [-1, n].
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "advect.h"
+
+namespace hermite {
+
+namespace {
+
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+template <int M, int R, int TX, int TY>
+struct KronShape {
+  static constexpr int P = 2 * M;
+  static constexpr int SX = (TY + 1) * M * M * R * TX;  // [node row][i3][i2][r1][x]
+  static constexpr int SY = TY * M * R * R * TX;        // [row][i3][r2][r1][x], two layers
+  static constexpr int SMEM_ELEMS = SX + 2 * SY;
+};
+
+template <typename TS, typename TC, int M, int R, int TX, int TY, int NT, bool WS>
+__global__ void __launch_bounds__(NT)
+    adv_kron_kernel(const TS *__restrict__ in, void *__restrict__ out_, Geom g, KronCoeffs<TC> co, int zchunk,
+                    int z0ws, int nzlws) {
+  using S = KronShape<M, R, TX, TY>;
+  constexpr int P = S::P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC *sX = reinterpret_cast<TC *>(smem_raw);
+  TC *sY = sX + S::SX;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, s = g.s;
+  const size_t N = (size_t)nx * ny * nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int zb = g.zlo + blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, g.zhi);
+  if (zb >= ze) return;  // uniform over the CTA
+  const int nl = ze - zb + 1;
+  for (int L = 0; L < nl; ++L) {
+    const int zn = wrap1(zb + s + L, nz);
+    // x-pass
+    for (int e = threadIdx.x; e < (TY + 1) * M * M * TX; e += NT) {
+      const int xc = e % TX;
+      int t = e / TX;
+      const int i2 = t % M;
+      t /= M;
+      const int i3 = t % M;
+      const int yn = t / M;
+      const int gx = x0 + xc;
+      if (gx >= nx || y0 + yn > ny) continue;
+      const int yg = wrap1(y0 + yn + s, ny);
+      const int xl = wrap1(gx + s, nx), xr = wrap1(gx + s + 1, nx);
+      const TS *base = in + (size_t)(i3 * M + i2) * M * N + ((size_t)zn * ny + yg) * nx;
+      TC v[P];
+#pragma unroll
+      for (int i1 = 0; i1 < M; ++i1) {
+        v[i1] = (TC)__ldg(base + (size_t)i1 * N + xl);
+        v[M + i1] = (TC)__ldg(base + (size_t)i1 * N + xr);
+      }
+      TC *dst = sX + ((yn * M + i3) * M + i2) * R * TX + xc;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        TC acc = co.g[0][r][0] * v[0];
+#pragma unroll
+        for (int c = 1; c < P; ++c) acc = fma(co.g[0][r][c], v[c], acc);
+        dst[r * TX] = acc;
+      }
+    }
+    __syncthreads();
+    // y-pass into layer buffer L & 1
+    TC *sYL = sY + (L & 1) * S::SY;
+    for (int e = threadIdx.x; e < TY * M * R * TX; e += NT) {
+      const int xc = e % TX;
+      int t = e / TX;
+      const int r1 = t % R;
+      t /= R;
+      const int i3 = t % M;
+      const int yc = t / M;
+      if (x0 + xc >= nx || y0 + yc >= ny) continue;
+      TC v[P];
+#pragma unroll
+      for (int side = 0; side < 2; ++side)
+#pragma unroll
+        for (int i2 = 0; i2 < M; ++i2) v[side * M + i2] = sX[((((yc + side) * M + i3) * M + i2) * R + r1) * TX + xc];
+      TC *dst = sYL + ((yc * M + i3) * R * R + r1) * TX + xc;
+#pragma unroll
+      for (int r2 = 0; r2 < R; ++r2) {
+        TC acc = co.g[1][r2][0] * v[0];
+#pragma unroll
+        for (int c = 1; c < P; ++c) acc = fma(co.g[1][r2][c], v[c], acc);
+        dst[r2 * R * TX] = acc;
+      }
+    }
+    __syncthreads();
+    if (L == 0) continue;
+    // z-pass of cell layer zb + L - 1 (layers L - 1 and L)
+    const TC *lo = sY + ((L - 1) & 1) * S::SY;
+    const int zc = zb + L - 1;
+    for (int e = threadIdx.x; e < TY * R * R * TX; e += NT) {
+      const int xc = e % TX;
+      int t = e / TX;
+      const int r1 = t % R;
+      t /= R;
+      const int r2 = t % R;
+      const int yc = t / R;
+      const int gx = x0 + xc, gy = y0 + yc;
+      if (gx >= nx || gy >= ny) continue;
+      TC v[P];
+#pragma unroll
+      for (int i3 = 0; i3 < M; ++i3) {
+        const int o = (((yc * M + i3) * R + r2) * R + r1) * TX + xc;
+        v[i3] = lo[o];
+        v[M + i3] = sYL[o];
+      }
+#pragma unroll
+      for (int r3 = 0; r3 < R; ++r3) {
+        TC acc = co.g[2][r3][0] * v[0];
+#pragma unroll
+        for (int c = 1; c < P; ++c) acc = fma(co.g[2][r3][c], v[c], acc);
+        if constexpr (WS) {
+          const size_t slab = (size_t)nzlws * ny * nx;
+          reinterpret_cast<TC *>(out_)[(size_t)((r3 * P + r2) * P + r1) * slab +
+                                       ((size_t)(zc - z0ws) * ny + gy) * nx + gx] = acc;
+        } else {
+          reinterpret_cast<TS *>(out_)[(size_t)((r3 * M + r2) * M + r1) * N + ((size_t)zc * ny + gy) * nx + gx] =
+              (TS)acc;
+        }
+      }
+    }
+  }
+}
+
+template <typename TS, typename TC, int M, int R, int TX, int TY, int NT, bool WS>
+cudaError_t launch_kron(const TS *in, void *out, const Geom &g, const KronCoeffs<TC> &co, int zchunk, int z0ws,
+                        int nzlws, cudaStream_t st) {
+  using S = KronShape<M, R, TX, TY>;
+  constexpr size_t smem = (size_t)S::SMEM_ELEMS * sizeof(TC);
+  static_assert(smem <= 227 * 1024, "shared memory of the tile");
+  auto kern = adv_kron_kernel<TS, TC, M, R, TX, TY, NT, WS>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nzc = g.zhi - g.zlo;
+  int zc = zchunk < 1 ? 1 : zchunk;
+  if ((nzc + zc - 1) / zc > 65535) zc = (nzc + 65534) / 65535;  // gridDim.z limit
+  if (nzc <= 0 || g.nx <= 0 || g.ny <= 0) return cudaSuccess;
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (nzc + zc - 1) / zc);
+  kern<<<grid, NT, smem, st>>>(in, out, g, co, zc, z0ws, nzlws);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace {
+
+// Alg. 4 on the cell polynomials of a slab, CB cells per CTA, then the
+// truncation to orders <= m (Sec. 2).  Shared memory holds three P^3 x CB
+// arrays [j][cell]: Ru, the current and the next Horner iterate.
+template <typename TS, typename TC, int M, int CB, int NT>
+__global__ void __launch_bounds__(NT)
+    adv_evolve_kernel(const TC *__restrict__ ws, TS *__restrict__ out, Geom g, int z0, int nzl, TC tau, TC ah0,
+                      TC ah1, TC ah2, int q) {
+  constexpr int P = 2 * M, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC *base = reinterpret_cast<TC *>(smem_raw);
+  TC *w = base + P3 * CB;
+  TC *w2 = w + P3 * CB;
+  const size_t ncell = (size_t)nzl * g.ny * g.nx;
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  const size_t c0 = (size_t)blockIdx.x * CB;
+  for (int e = threadIdx.x; e < P3 * CB; e += NT) {
+    const int k = e % CB, j = e / CB;
+    const size_t c = c0 + k;
+    const TC v = c < ncell ? ws[(size_t)j * ncell + c] : TC(0);
+    base[e] = v;
+    w[e] = v;
+  }
+  __syncthreads();
+  for (int stage = q; stage >= 1; --stage) {  // w <- Ru + (tau / k) L w
+    const TC f = tau / (TC)stage;
+    const TC f0 = f * ah0, f1 = f * ah1, f2 = f * ah2;
+    for (int e = threadIdx.x; e < P3 * CB; e += NT) {
+      const int k = e % CB, j = e / CB;
+      const int jx = j % P, jy = (j / P) % P, jz = j / (P * P);
+      TC d = TC(0);
+      if (jx + 1 < P) d = fma(f0 * (TC)(jx + 1), w[(j + 1) * CB + k], d);
+      if (jy + 1 < P) d = fma(f1 * (TC)(jy + 1), w[(j + P) * CB + k], d);
+      if (jz + 1 < P) d = fma(f2 * (TC)(jz + 1), w[(j + P * P) * CB + k], d);
+      w2[e] = base[e] + d;
+    }
+    __syncthreads();
+    TC *t = w;
+    w = w2;
+    w2 = t;
+  }
+  for (int e = threadIdx.x; e < M * M * M * CB; e += NT) {
+    const int k = e % CB, i = e / CB;
+    const size_t c = c0 + k;
+    if (c >= ncell) continue;
+    const int i1 = i % M, i2 = (i / M) % M, i3 = i / (M * M);
+    out[(size_t)i * N + (size_t)z0 * g.ny * g.nx + c] = (TS)w[((i3 * P + i2) * P + i1) * CB + k];
+  }
+}
+
+template <typename TS, typename TC, int M, int CB, int NT>
+cudaError_t launch_evolve_adv(const TC *ws, TS *out, const Geom &g, int z0, int nzl, const AdvEvolveParams &ep,
+                              cudaStream_t st) {
+  constexpr int P = 2 * M;
+  constexpr size_t smem = (size_t)3 * P * P * P * CB * sizeof(TC);
+  static_assert(smem <= 227 * 1024, "shared memory of the evolution kernel");
+  auto kern = adv_evolve_kernel<TS, TC, M, CB, NT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const size_t ncell = (size_t)nzl * g.ny * g.nx;
+  if (ncell == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((ncell + CB - 1) / CB);
+  kern<<<blocks, NT, smem, st>>>(ws, out, g, z0, nzl, (TC)ep.tau, (TC)ep.ah[0], (TC)ep.ah[1], (TC)ep.ah[2], ep.q);
+  return cudaGetLastError();
+}
+
+// Tile tables.  Fused (R = M): TX = 32 cells along x1; TY = 4 / 2 / 2 rows in
+// FP64 and 8 / 4 / 2 in FP32 (m = 1 / 2 / 3) keep the CTA within 27-115 KB of
+// shared memory.  Interpolation (R = P): TY = 4 / 2 / 1.
+template <typename TS, typename TC>
+cudaError_t fused_dispatch(int m, const void *in, void *out, const Geom &g, const KronCoeffs<TC> &co, int zchunk,
+                           cudaStream_t st) {
+  const TS *i = static_cast<const TS *>(in);
+  constexpr bool d = sizeof(TC) == 8;
+  switch (m) {
+    case 1: return launch_kron<TS, TC, 2, 2, 32, d ? 4 : 8, 256, false>(i, out, g, co, zchunk, 0, 0, st);
+    case 2: return launch_kron<TS, TC, 3, 3, 32, d ? 2 : 4, 256, false>(i, out, g, co, zchunk, 0, 0, st);
+    case 3: return launch_kron<TS, TC, 4, 4, 32, 2, 256, false>(i, out, g, co, zchunk, 0, 0, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename TS, typename TC>
+cudaError_t interp_dispatch(int m, const void *in, void *ws, const Geom &g, int z0, int nzl, const KronCoeffs<TC> &co,
+                            cudaStream_t st) {
+  const TS *i = static_cast<const TS *>(in);
+  Geom gs = g;
+  gs.zlo = z0;
+  gs.zhi = z0 + nzl;
+  const int zc = nzl < 16 ? nzl : 16;
+  switch (m) {
+    case 1: return launch_kron<TS, TC, 2, 4, 32, 4, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
+    case 2: return launch_kron<TS, TC, 3, 6, 32, 2, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
+    case 3: return launch_kron<TS, TC, 4, 8, 32, 1, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename TS, typename TC>
+cudaError_t evolve_dispatch(int m, const void *ws, void *out, const Geom &g, int z0, int nzl,
+                            const AdvEvolveParams &ep, cudaStream_t st) {
+  const TC *w = static_cast<const TC *>(ws);
+  TS *o = static_cast<TS *>(out);
+  switch (m) {
+    case 1: return launch_evolve_adv<TS, TC, 2, 32, 256>(w, o, g, z0, nzl, ep, st);
+    case 2: return launch_evolve_adv<TS, TC, 3, 16, 256>(w, o, g, z0, nzl, ep, st);
+    case 3: return launch_evolve_adv<TS, TC, 4, 8, 256>(w, o, g, z0, nzl, ep, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_adv_fused(int m, int state, int compute, const void *in, void *out, const Geom &g,
+                             const KronCoeffs<double> &cd, const KronCoeffs<float> &cf, int zchunk, cudaStream_t st) {
+  if (compute == kF64) return fused_dispatch<double, double>(m, in, out, g, cd, zchunk, st);
+  if (state == kF64) return fused_dispatch<double, float>(m, in, out, g, cf, zchunk, st);
+  return fused_dispatch<float, float>(m, in, out, g, cf, zchunk, st);
+}
+
+cudaError_t launch_adv_interp(int m, int state, int compute, const void *in, void *ws, const Geom &g, int z0, int nzl,
+                              const KronCoeffs<double> &cd, const KronCoeffs<float> &cf, cudaStream_t st) {
+  if (compute == kF64) return interp_dispatch<double, double>(m, in, ws, g, z0, nzl, cd, st);
+  if (state == kF64) return interp_dispatch<double, float>(m, in, ws, g, z0, nzl, cf, st);
+  return interp_dispatch<float, float>(m, in, ws, g, z0, nzl, cf, st);
+}
+
+cudaError_t launch_adv_evolve(int m, int state, int compute, const void *ws, void *out, const Geom &g, int z0,
+                              int nzl, const AdvEvolveParams &ep, cudaStream_t st) {
+  if (compute == kF64) return evolve_dispatch<double, double>(m, ws, out, g, z0, nzl, ep, st);
+  if (state == kF64) return evolve_dispatch<double, float>(m, ws, out, g, z0, nzl, ep, st);
+  return evolve_dispatch<float, float>(m, ws, out, g, z0, nzl, ep, st);
+}
+
+// Host tables.  Shift(sigma) maps the monomial coefficients b_j of p(xi) to
+// those of p(xi + sigma): sum_{j >= r} C(j, r) sigma^(j - r) b_j (binomial
+// expansion); the fused factor keeps the rows r <= m.
+void build_adv_coeffs(int m, const double h[3], const double a[3], double tau, KronCoeffs<double> *fused,
+                      KronCoeffs<double> *interp) {
+  const int M = m + 1, P = 2 * M;
+  double H[64];
+  build_H(m, H);
+  *fused = KronCoeffs<double>{};
+  *interp = KronCoeffs<double>{};
+  for (int k = 0; k < 3; ++k) {
+    const long double sigma = (long double)a[k] * tau / h[k];
+    for (int r = 0; r < M; ++r)
+      for (int c = 0; c < P; ++c) {
+        long double acc = 0.0L, binom = 1.0L, pw = 1.0L;  // C(j, r), sigma^(j - r) at j = r
+        for (int j = r; j < P; ++j) {
+          acc += binom * pw * (long double)H[j * P + c];
+          binom = binom * (j + 1) / (j + 1 - r);
+          pw *= sigma;
+        }
+        fused->g[k][r][c] = (double)acc;
+      }
+    for (int r = 0; r < P; ++r)
+      for (int c = 0; c < P; ++c) interp->g[k][r][c] = H[r * P + c];
+  }
+}
+
+}  // namespace hermite

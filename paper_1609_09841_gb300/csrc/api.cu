@@ -146,10 +146,60 @@ int ensure_red(hermite_plan_s *p) {
   return HERMITE_OK;
 }
 
+// Advection (Eq. 1 with a constant velocity a): largest max_k |a_k| tau / h_k
+// per order m and Taylor order q, the smaller of the limits of the Fourier
+// symbol for a mode along x1 (a along x1) and for the diagonal (a = (1, 1, 1)
+// direction, 7^3 theta grid), rounded down to two decimals.  With the whole
+// series (q = 3(2m+1)) the half step is a Kronecker product of 1-D maps and the
+// limit is the half cell of Sec. 2; q = 1 (forward Euler) has no stable step.
+const double kAdvLimit[4][kMaxQ + 1] = {
+    {0},
+    {0, 0.01, 0.16, 0.25, 0.31, 0.37, 0.42, 0.45, 0.48, 0.50},
+    {0, 0.00, 0.03, 0.15, 0.20, 0.18, 0.23, 0.26, 0.29, 0.34, 0.38, 0.41, 0.46, 0.48, 0.49, 0.50},
+    {0, 0.00, 0.00, 0.10, 0.14, 0.05, 0.13, 0.16, 0.19, 0.23, 0.26, 0.28, 0.29, 0.32, 0.35, 0.39,
+     0.41, 0.44, 0.47, 0.49, 0.49, 0.50},
+};
+
+double adv_limit_of(int m, int q) {
+  return (m >= 1 && m <= 3 && q >= 1 && q <= 3 * (2 * m + 1)) ? kAdvLimit[m][q] : 0.0;
+}
+
+// Advection half step: the fused Kronecker kernel (whole series), or the
+// split pair (interpolation to the workspace, Alg. 4) z-slab by z-slab.
+int run_adv_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaStream_t st, int zlo, int zhi) {
+  Geom g = geom_of(p, parity == 0 ? 0 : -1);
+  if (zhi >= 0) {
+    g.zlo = zlo;
+    g.zhi = zhi;
+  }
+  const int compute = p->prec == HERMITE_FP64 ? kF64 : kF32;
+  const int state = p->state == HERMITE_STATE_FP64 ? kF64 : kF32;
+  cudaError_t e;
+  if (p->variant != HERMITE_SPLIT) {
+    e = launch_adv_fused(p->m, state, compute, in, out, g, p->adv_fused, p->adv_fused32, p->zchunk, st);
+    return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "advection half-step launch");
+  }
+  const int P = 2 * p->m + 2;
+  const size_t elt = compute == kF64 ? sizeof(double) : sizeof(float);
+  const size_t per_layer = (size_t)P * P * P * p->n[0] * p->n[1] * elt;
+  const int nzl = (int)std::max<size_t>(1, std::min<size_t>((size_t)(g.zhi - g.zlo), p->ws_limit / per_layer));
+  int rc = ensure_ws(p, per_layer * nzl);
+  if (rc) return rc;
+  for (int z0 = g.zlo; z0 < g.zhi; z0 += nzl) {
+    const int nl = std::min(nzl, g.zhi - z0);
+    e = launch_adv_interp(p->m, state, compute, in, p->ws, g, z0, nl, p->adv_interp, p->adv_interp32, st);
+    if (e != cudaSuccess) return cuda_fail(e, "advection interpolation launch");
+    e = launch_adv_evolve(p->m, state, compute, p->ws, out, g, z0, nl, p->adv_ev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "advection evolution launch");
+  }
+  return HERMITE_OK;
+}
+
 // Device-pointer half step of either direction (adjoint: transposed tables,
 // mirrored corner offset).
 int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st, int zlo = 0,
              int zhi = -1) {
+  if (p->eq == 1) return run_adv_step(p, in, out, parity, st, zlo, zhi);
   const int s_fwd = parity == 0 ? 0 : -1;
   const bool adjoint = mode == kAdjoint;
   const int s = adjoint ? -s_fwd - 1 : s_fwd;
@@ -375,8 +425,76 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
   return HERMITE_OK;
 }
 
+double hermite_adv_stability_limit(int m, int q) { return adv_limit_of(m, q == 0 ? 3 * (2 * m + 1) : q); }
+
+int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], const double a[3], double dt,
+                     int q, int prec, int state_dtype, int variant) {
+  g_last_error.clear();
+  if (!out) return fail(HERMITE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || m > 3) return fail(HERMITE_EINVAL, "order m = %d not in 1..3", m);
+  if (!grid || !h || !a) return fail(HERMITE_EINVAL, "grid, h or a is NULL");
+  for (int k = 0; k < 3; ++k) {
+    if (grid[k] < 1 || grid[k] > (1 << 20)) return fail(HERMITE_EINVAL, "grid[%d] = %d out of range", k, grid[k]);
+    if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(HERMITE_EINVAL, "h[%d] must be positive", k);
+    if (!std::isfinite(a[k])) return fail(HERMITE_EINVAL, "velocity a[%d] is not finite", k);
+  }
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
+  const int qfull = 3 * (2 * m + 1);
+  if (q == 0) q = qfull;
+  if (q < 1 || q > qfull) return fail(HERMITE_EINVAL, "q = %d outside 1..%d (3(2m+1)) for order %d", q, qfull, m);
+  if (prec != HERMITE_FP64 && prec != HERMITE_FP32)
+    return fail(HERMITE_EUNSUPPORTED, "advection runs in FP64 or FP32 arithmetic");
+  if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
+    return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
+  if (prec == HERMITE_FP64 && state_dtype != HERMITE_STATE_FP64)
+    return fail(HERMITE_EUNSUPPORTED, "FP64 arithmetic needs an FP64 state");
+  if (variant != HERMITE_AUTO && variant != HERMITE_FUSED && variant != HERMITE_SPLIT)
+    return fail(HERMITE_EINVAL, "variant %d unknown", variant);
+  if (variant == HERMITE_AUTO) variant = q == qfull ? HERMITE_FUSED : HERMITE_SPLIT;
+  if (variant == HERMITE_FUSED && q != qfull)
+    return fail(HERMITE_EUNSUPPORTED, "the fused advection kernel runs the whole series (q = %d) only", qfull);
+  const double tau = 0.5 * dt;
+  for (int k = 0; k < 3; ++k) {
+    const double lam = std::fabs(a[k]) * tau / h[k];
+    if (lam > adv_limit_of(m, q) * (1.0 + 1e-12))
+      return fail(HERMITE_EUNSTABLE, "|a[%d]|*(dt/2)/h[%d] = %.6g above the stability limit %.3g of order %d, q = %d",
+                  k, k, lam, adv_limit_of(m, q), m, q);
+  }
+  hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
+  if (!p) return fail(HERMITE_ENOMEM, "plan allocation");
+  p->eq = 1;
+  p->m = m;
+  for (int k = 0; k < 3; ++k) {
+    p->n[k] = grid[k];
+    p->h[k] = h[k];
+    p->a[k] = a[k];
+  }
+  p->c = 0.0;
+  p->dt = dt;
+  p->tau = tau;
+  p->prec = prec;
+  p->q = q;
+  p->state = state_dtype;
+  p->variant = variant;
+  p->elems = (size_t)(m + 1) * (m + 1) * (m + 1) * grid[0] * grid[1] * grid[2];
+  build_H(m, p->H);
+  build_adv_coeffs(m, h, a, tau, &p->adv_fused, &p->adv_interp);
+  p->adv_fused32 = cast_kron<float>(p->adv_fused);
+  p->adv_interp32 = cast_kron<float>(p->adv_interp);
+  p->adv_ev.tau = tau;
+  for (int k = 0; k < 3; ++k) p->adv_ev.ah[k] = a[k] / h[k];
+  p->adv_ev.q = q;
+  p->tile = 0;
+  p->zchunk = 16;
+  p->ws_limit = (size_t)1 << 30;
+  *out = p;
+  return HERMITE_OK;
+}
+
 int hermite_set_taylor_order(hermite_plan_t p, int q) {
   if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "advection plans fix q at hermite_adv_plan");
   if (q < 4 || q > 3 * (2 * p->m + 1))
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * p->m + 1), p->m);
   if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF))
@@ -394,6 +512,7 @@ size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
 
 int hermite_schedule_count(hermite_plan_t p) {
   if (!p || p->batch) return 0;
+  if (p->eq) return 1;
   if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
   return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
 }
@@ -433,6 +552,7 @@ int hermite_step(hermite_plan_t p, const void *in, void *out, int parity, void *
 
 int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, int parity, void *stream) {
   if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "no adjoint for advection plans");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   int rc = check_device_pair(p, out_adj, in_adj);
@@ -444,6 +564,7 @@ int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, in
 
 int hermite_step_dc(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
   if (!p) return fail(HERMITE_EINVAL, "plan is NULL");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "dS/dc is defined for the wave equation only");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   int rc = check_device_pair(p, in, out);
@@ -456,6 +577,7 @@ int hermite_step_dc(hermite_plan_t p, const void *in, void *out, int parity, voi
 int hermite_record(hermite_plan_t p, const void *state, const long long *idx, int count, double *out,
                    void *stream) {
   if (!p || !state || !idx || !out) return fail(HERMITE_EINVAL, "null argument");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "receivers are defined for the wave equation only");
   if (count < 0) return fail(HERMITE_EINVAL, "negative receiver count");
   if (count == 0) return HERMITE_OK;
   cudaError_t e = launch_record(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, state, idx, count, out,
@@ -465,6 +587,7 @@ int hermite_record(hermite_plan_t p, const void *state, const long long *idx, in
 
 int hermite_inject(hermite_plan_t p, void *adj, const long long *idx, int count, const double *w, void *stream) {
   if (!p || !adj || !idx || !w) return fail(HERMITE_EINVAL, "null argument");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "receivers are defined for the wave equation only");
   if (count < 0) return fail(HERMITE_EINVAL, "negative receiver count");
   if (count == 0) return HERMITE_OK;
   cudaError_t e = launch_inject(p->state == HERMITE_STATE_FP64 ? kF64 : kF32, adj, idx, count, w,
@@ -477,6 +600,7 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
   if (!p || !state || !ref || !out) return fail(HERMITE_EINVAL, "null argument");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan");
   if ((mask & 3u) == 0) return fail(HERMITE_EINVAL, "component mask selects no field");
+  if (p->eq && (mask & 2u)) return fail(HERMITE_EINVAL, "an advection state has one field (mask bit 1 only)");
   if (classify(state) != kDevicePtr || classify(ref) != kDevicePtr)
     return fail(HERMITE_EINVAL, "hermite_error takes device buffers");
   cudaStream_t st = (cudaStream_t)stream;

@@ -5,6 +5,7 @@
 
 #include <string>
 
+#include "advect.h"
 #include "hermite_impl.h"
 
 namespace hermite {
@@ -28,6 +29,11 @@ struct hermite_plan_s {
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
   int q = 4;                // Taylor stages of the local evolution (4 = RK4)
+  int eq = 0;               // equation: 0 the scalar wave equation, 1 advection (Eq. 1)
+  double a[3] = {0, 0, 0};  // advection velocity
+  hermite::KronCoeffs<double> adv_fused, adv_interp;     // advection: 1-D factors (FP64)
+  hermite::KronCoeffs<float> adv_fused32, adv_interp32;  // and their FP32 roundings
+  hermite::AdvEvolveParams adv_ev;                       // advection: split evolution constants
   int tile;                 // fused kernel: index of the compiled tile shape
   int zchunk;               // fused kernel: cells per CTA along x3
   size_t ws_limit;          // split variant: workspace budget in bytes

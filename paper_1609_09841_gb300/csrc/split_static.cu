@@ -65,6 +65,7 @@ size_t hermite_static_workspace_bytes(void) { return kStaticBytes; }
 
 int hermite_step_split_static(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
   if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
+  if (p->eq) return fail(HERMITE_EUNSUPPORTED, "the allocation-free step is for wave-equation plans");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
   if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
   if (p->prec != HERMITE_FP64 && p->prec != HERMITE_FP32)

@@ -168,3 +168,37 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def adv_stability_limit(m, q=0):
+    """Largest max_k |a_k| (dt/2)/h_k of a stable advection half step (q = 0:
+    the whole series, limit 0.5)."""
+    return capi.lib.hermite_adv_stability_limit(int(m), int(q))
+
+
+class AdvectionPlan(Plan):
+    """Half-step plan of the advection equation u_t = a . grad u (Eq. 1 is
+    a = (1, 1, 1)): order m, periodic grid, spacings h, velocity a, FULL time
+    step dt and q Taylor stages (0 = the whole series 3(2m+1), run by the fused
+    kernel; fewer stages run the split pair)."""
+
+    def __init__(self, m, grid, h, a, dt, q=0, prec="fp64", state="fp64", variant="auto"):
+        self.m, self.grid, self.h = int(m), tuple(int(v) for v in grid), tuple(float(v) for v in h)
+        self.a = tuple(float(v) for v in a)
+        self.c, self.dt, self.prec, self.state, self.variant = 0.0, float(dt), prec, state, variant
+        self.q = int(q) if q else 3 * (2 * self.m + 1)
+        handle = ctypes.c_void_p()
+        capi.check(capi.lib.hermite_adv_plan(ctypes.byref(handle), self.m, (ctypes.c_int * 3)(*self.grid),
+                                             (ctypes.c_double * 3)(*self.h), (ctypes.c_double * 3)(*self.a),
+                                             self.dt, int(q), PRECISIONS[prec], STATES[state], VARIANTS[variant]))
+        self._h = handle
+
+    @property
+    def shape(self):
+        M = self.m + 1
+        return (M, M, M, self.grid[2], self.grid[1], self.grid[0])
+
+    def error(self, x, ref, mask=0b101, stream=None):
+        """(max_abs, max_rel, rms, l2_rel) of x - ref (one field; mask bit 4:
+        every derivative component, else values only)."""
+        return super().error(x, ref, mask, stream)
