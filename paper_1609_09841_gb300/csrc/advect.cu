@@ -26,20 +26,22 @@ namespace {
 
 __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-template <int M, int R, int TX, int TY>
+template <typename TS, typename TC, int M, int R, int TX, int TY>
 struct KronShape {
   static constexpr int P = 2 * M;
   static constexpr int SX = (TY + 1) * M * M * R * TX;  // [node row][i3][i2][r1][x]
   static constexpr int SY = TY * M * R * R * TX;        // [row][i3][r2][r1][x], two layers
-  static constexpr int SMEM_ELEMS = SX + 2 * SY;
+  static constexpr size_t BYTES = ((size_t)SX + 2 * SY) * sizeof(TC);
 };
 
 template <typename TS, typename TC, int M, int R, int TX, int TY, int NT, bool WS>
 __global__ void __launch_bounds__(NT)
     adv_kron_kernel(const TS *__restrict__ in, void *__restrict__ out_, Geom g, KronCoeffs<TC> co, int zchunk,
                     int z0ws, int nzlws) {
-  using S = KronShape<M, R, TX, TY>;
+  using S = KronShape<TS, TC, M, R, TX, TY>;
   constexpr int P = S::P;
+  constexpr int XI = (TY + 1) * M * M * TX;  // x-pass items per layer: (node row, i3, i2, x)
+  constexpr int IT = (XI + NT - 1) / NT;     // per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC *sX = reinterpret_cast<TC *>(smem_raw);
   TC *sY = sX + S::SX;
@@ -50,36 +52,55 @@ __global__ void __launch_bounds__(NT)
   const int ze = min(zb + zchunk, g.zhi);
   if (zb >= ze) return;  // uniform over the CTA
   const int nl = ze - zb + 1;
-  for (int L = 0; L < nl; ++L) {
+  // The x-pass inputs of one node layer, held in registers: the loads of
+  // layer L+1 are issued before the y- and z-passes of layer L so that their
+  // latency overlaps that work.
+  TS pre[IT][P];
+  auto load = [&](int L) {
     const int zn = wrap1(zb + s + L, nz);
-    // x-pass
-    for (int e = threadIdx.x; e < (TY + 1) * M * M * TX; e += NT) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int e = threadIdx.x + it * NT;
       const int xc = e % TX;
       int t = e / TX;
       const int i2 = t % M;
       t /= M;
       const int i3 = t % M;
       const int yn = t / M;
-      const int gx = x0 + xc;
-      if (gx >= nx || y0 + yn > ny) continue;
+      if (e >= XI || x0 + xc >= nx || y0 + yn > ny) continue;
       const int yg = wrap1(y0 + yn + s, ny);
-      const int xl = wrap1(gx + s, nx), xr = wrap1(gx + s + 1, nx);
+      const int xl = wrap1(x0 + xc + s, nx), xr = wrap1(x0 + xc + s + 1, nx);
       const TS *base = in + (size_t)(i3 * M + i2) * M * N + ((size_t)zn * ny + yg) * nx;
-      TC v[P];
 #pragma unroll
       for (int i1 = 0; i1 < M; ++i1) {
-        v[i1] = (TC)__ldg(base + (size_t)i1 * N + xl);
-        v[M + i1] = (TC)__ldg(base + (size_t)i1 * N + xr);
+        pre[it][i1] = __ldg(base + (size_t)i1 * N + xl);
+        pre[it][M + i1] = __ldg(base + (size_t)i1 * N + xr);
       }
+    }
+  };
+  load(0);
+  for (int L = 0; L < nl; ++L) {
+    // x-pass from the registers
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int e = threadIdx.x + it * NT;
+      const int xc = e % TX;
+      int t = e / TX;
+      const int i2 = t % M;
+      t /= M;
+      const int i3 = t % M;
+      const int yn = t / M;
+      if (e >= XI || x0 + xc >= nx || y0 + yn > ny) continue;
       TC *dst = sX + ((yn * M + i3) * M + i2) * R * TX + xc;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        TC acc = co.g[0][r][0] * v[0];
+        TC acc = co.g[0][r][0] * (TC)pre[it][0];
 #pragma unroll
-        for (int c = 1; c < P; ++c) acc = fma(co.g[0][r][c], v[c], acc);
+        for (int c = 1; c < P; ++c) acc = fma(co.g[0][r][c], (TC)pre[it][c], acc);
         dst[r * TX] = acc;
       }
     }
+    if (L + 1 < nl) load(L + 1);
     __syncthreads();
     // y-pass into layer buffer L & 1
     TC *sYL = sY + (L & 1) * S::SY;
@@ -147,8 +168,8 @@ __global__ void __launch_bounds__(NT)
 template <typename TS, typename TC, int M, int R, int TX, int TY, int NT, bool WS>
 cudaError_t launch_kron(const TS *in, void *out, const Geom &g, const KronCoeffs<TC> &co, int zchunk, int z0ws,
                         int nzlws, cudaStream_t st) {
-  using S = KronShape<M, R, TX, TY>;
-  constexpr size_t smem = (size_t)S::SMEM_ELEMS * sizeof(TC);
+  using S = KronShape<TS, TC, M, R, TX, TY>;
+  constexpr size_t smem = S::BYTES;
   static_assert(smem <= 227 * 1024, "shared memory of the tile");
   auto kern = adv_kron_kernel<TS, TC, M, R, TX, TY, NT, WS>;
   static bool attr = false;
@@ -163,6 +184,166 @@ cudaError_t launch_kron(const TS *in, void *out, const Geom &g, const KronCoeffs
   if (nzc <= 0 || g.nx <= 0 || g.ny <= 0) return cudaSuccess;
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (nzc + zc - 1) / zc);
   kern<<<grid, NT, smem, st>>>(in, out, g, co, zc, z0ws, nzlws);
+  return cudaGetLastError();
+}
+
+// Fused half step (R = M), the hot advection kernel.  Same three passes as
+// adv_kron_kernel, but
+//   * one y-pass layer in shared memory: each node layer is the upper face of
+//     the cell below it and the lower face of the cell above it, so the
+//     z-pass finishes the pending cell (upper-face columns of Gz) and starts
+//     the next one (lower-face columns) from the same layer, keeping the
+//     partial sums of its column in registers;
+//   * NT = TY * M * TX threads: in the y- and z-passes a thread owns one
+//     (row, component, x) column for the whole walk along x3, so its indices
+//     are computed once, and loops over the last component index.
+template <typename TS, typename TC, int M, int TX, int TY>
+struct FusedAdvShape {
+  static constexpr int P = 2 * M;
+  static constexpr int NT = TY * M * TX;
+  static constexpr int SX = (TY + 1) * M * M * M * TX;  // [node row][i3][i2][r1][x]
+  static constexpr int SY = TY * M * M * M * TX;        // [row][i3][r2][r1][x], one layer
+  static constexpr size_t BYTES = ((size_t)SX + SY) * sizeof(TC);
+};
+
+template <typename TS, typename TC, int M, int TX, int TY, int XC>
+__global__ void __launch_bounds__(TY * M * TX)
+    adv_fused_kernel(const TS *__restrict__ in, TS *__restrict__ out, Geom g, KronCoeffs<TC> co, int zchunk) {
+  using S = FusedAdvShape<TS, TC, M, TX, TY>;
+  constexpr int P = S::P, NT = S::NT;
+  constexpr int XI = (TY + 1) * M * M * TX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC *sX = reinterpret_cast<TC *>(smem_raw);
+  TC *sY = sX + S::SX;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, s = g.s;
+  const size_t N = (size_t)nx * ny * nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int zb = g.zlo + blockIdx.z * zchunk;
+  const int ze = min(zb + zchunk, g.zhi);
+  if (zb >= ze) return;  // uniform over the CTA
+  const int nl = ze - zb + 1;
+  // this thread's column: x = xc, row = yc, and component k (i3 in the
+  // y-pass, r2 in the z-pass)
+  const int xc = threadIdx.x % TX;
+  const int k = (threadIdx.x / TX) % M;
+  const int yc = threadIdx.x / (TX * M);
+  const bool live = x0 + xc < nx && y0 + yc < ny;
+  const size_t out_col = (size_t)(k * M) * N + (size_t)(y0 + yc) * nx + (x0 + xc);  // r2 = k
+  // NT is a multiple of TX, so every x-pass item of this thread has x = xc
+  constexpr int IT = (XI + NT - 1) / NT;
+  const bool xin = x0 + xc < nx;
+  const int xl = wrap1(x0 + xc + s, nx), xr = wrap1(x0 + xc + s + 1, nx);
+  TC acc[M][M];  // pending cell: [r1][r3]
+  for (int L = 0; L < nl; ++L) {
+    const int zn = wrap1(zb + s + L, nz);
+    // x-pass: items (node row, i3, i2, x), IT per thread, taken in chunks of
+    // XC items whose loads are all issued before the first product
+#pragma unroll
+    for (int i0 = 0; i0 < IT; i0 += XC) {
+      TS v[XC][P];
+#pragma unroll
+      for (int j = 0; j < XC; ++j) {
+        const int e = threadIdx.x + (i0 + j) * NT;
+        const int t = e / TX;
+        const int i2 = t % M, i3 = (t / M) % M, yn = t / (M * M);
+        if (i0 + j >= IT || e >= XI || !xin || y0 + yn > ny) continue;
+        const int yg = wrap1(y0 + yn + s, ny);
+        const TS *base = in + (size_t)(i3 * M + i2) * M * N + ((size_t)zn * ny + yg) * nx;
+#pragma unroll
+        for (int i1 = 0; i1 < M; ++i1) {
+          v[j][i1] = __ldg(base + (size_t)i1 * N + xl);
+          v[j][M + i1] = __ldg(base + (size_t)i1 * N + xr);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < XC; ++j) {
+        const int e = threadIdx.x + (i0 + j) * NT;
+        const int t = e / TX;
+        const int i2 = t % M, i3 = (t / M) % M, yn = t / (M * M);
+        if (i0 + j >= IT || e >= XI || !xin || y0 + yn > ny) continue;
+        TC *dst = sX + ((yn * M + i3) * M + i2) * M * TX + xc;
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          TC a = co.g[0][r][0] * (TC)v[j][0];
+#pragma unroll
+          for (int c = 1; c < P; ++c) a = fma(co.g[0][r][c], (TC)v[j][c], a);
+          dst[r * TX] = a;
+        }
+      }
+    }
+    __syncthreads();
+    // y-pass: column (yc, i3 = k, x), loop over r1
+    if (live) {
+#pragma unroll
+      for (int r1 = 0; r1 < M; ++r1) {
+        TC v[P];
+#pragma unroll
+        for (int side = 0; side < 2; ++side)
+#pragma unroll
+          for (int i2 = 0; i2 < M; ++i2) v[side * M + i2] = sX[((((yc + side) * M + k) * M + i2) * M + r1) * TX + xc];
+        TC *dst = sY + ((yc * M + k) * M * M + r1) * TX + xc;
+#pragma unroll
+        for (int r2 = 0; r2 < M; ++r2) {
+          TC a = co.g[1][r2][0] * v[0];
+#pragma unroll
+          for (int c = 1; c < P; ++c) a = fma(co.g[1][r2][c], v[c], a);
+          dst[r2 * M * TX] = a;
+        }
+      }
+    }
+    __syncthreads();
+    // z-pass: column (yc, r2 = k, x), loop over r1; this layer is the upper
+    // face of cell zb + L - 1 and the lower face of cell zb + L
+    if (live) {
+      const size_t zoff = (size_t)(zb + L - 1) * ny * nx;
+#pragma unroll
+      for (int r1 = 0; r1 < M; ++r1) {
+        TC v[M];
+#pragma unroll
+        for (int i3 = 0; i3 < M; ++i3) v[i3] = sY[(((yc * M + i3) * M + k) * M + r1) * TX + xc];
+        if (L > 0) {
+#pragma unroll
+          for (int r3 = 0; r3 < M; ++r3) {
+            TC a = acc[r1][r3];
+#pragma unroll
+            for (int i3 = 0; i3 < M; ++i3) a = fma(co.g[2][r3][M + i3], v[i3], a);
+            out[out_col + (size_t)(r3 * M * M + r1) * N + zoff] = (TS)a;
+          }
+        }
+#pragma unroll
+        for (int r3 = 0; r3 < M; ++r3) {
+          TC a = co.g[2][r3][0] * v[0];
+#pragma unroll
+          for (int i3 = 1; i3 < M; ++i3) a = fma(co.g[2][r3][i3], v[i3], a);
+          acc[r1][r3] = a;
+        }
+      }
+    }
+    // the next x-pass writes sX (read by this y-pass: behind the barrier
+    // above) and the next y-pass writes sY after the next barrier
+  }
+}
+
+template <typename TS, typename TC, int M, int TX, int TY, int XC>
+cudaError_t launch_fused_adv(const TS *in, TS *out, const Geom &g, const KronCoeffs<TC> &co, int zchunk,
+                             cudaStream_t st) {
+  using S = FusedAdvShape<TS, TC, M, TX, TY>;
+  constexpr size_t smem = S::BYTES;
+  static_assert(smem <= 227 * 1024, "shared memory of the tile");
+  static_assert(S::NT <= 1024, "threads per CTA");
+  auto kern = adv_fused_kernel<TS, TC, M, TX, TY, XC>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int nzc = g.zhi - g.zlo;
+  int zc = zchunk < 1 ? 1 : zchunk;
+  if ((nzc + zc - 1) / zc > 65535) zc = (nzc + 65534) / 65535;  // gridDim.z limit
+  if (nzc <= 0 || g.nx <= 0 || g.ny <= 0) return cudaSuccess;
+  dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (nzc + zc - 1) / zc);
+  kern<<<grid, S::NT, smem, st>>>(in, out, g, co, zc);
   return cudaGetLastError();
 }
 
@@ -239,26 +420,45 @@ cudaError_t launch_evolve_adv(const TC *ws, TS *out, const Geom &g, int z0, int 
   return cudaGetLastError();
 }
 
-// Tile tables.  Fused (R = M): TX = 32 cells along x1; TY = 4 / 2 / 2 rows in
-// FP64 and 8 / 4 / 2 in FP32 (m = 1 / 2 / 3) keep the CTA within 27-115 KB of
-// shared memory.  Interpolation (R = P): TY = 4 / 2 / 1.
-template <typename TS, typename TC>
-cudaError_t fused_dispatch(int m, const void *in, void *out, const Geom &g, const KronCoeffs<TC> &co, int zchunk,
-                           cudaStream_t st) {
-  const TS *i = static_cast<const TS *>(in);
+// Tile tables (TX x TY cells per CTA), two shapes per order and precision
+// for the fused kernel (the plan's schedule picks one) and one for the
+// interpolation kernel; every shape stays within 227 KB of shared memory
+// (checked at compile time).
+template <typename TS, typename TC, int XC>
+cudaError_t fused_dispatch_xc(int m, bool b, const TS *i, TS *o, const Geom &g, const KronCoeffs<TC> &co, int zchunk,
+                              cudaStream_t st) {
   constexpr bool d = sizeof(TC) == 8;
+  // TY rows per CTA (threads TY * M * 32): FP32 8|16, 4|8, 2|4; FP64 4|8, 2|4, 1|2 (m = 1, 2, 3)
   switch (m) {
-    case 1: return launch_kron<TS, TC, 2, 2, 32, d ? 4 : 8, 256, false>(i, out, g, co, zchunk, 0, 0, st);
-    case 2: return launch_kron<TS, TC, 3, 3, 32, d ? 2 : 4, 256, false>(i, out, g, co, zchunk, 0, 0, st);
-    case 3: return launch_kron<TS, TC, 4, 4, 32, 2, 256, false>(i, out, g, co, zchunk, 0, 0, st);
+    case 1:
+      return b ? launch_fused_adv<TS, TC, 2, 32, d ? 8 : 16, XC>(i, o, g, co, zchunk, st)
+               : launch_fused_adv<TS, TC, 2, 32, d ? 4 : 8, XC>(i, o, g, co, zchunk, st);
+    case 2:
+      return b ? launch_fused_adv<TS, TC, 3, 32, d ? 4 : 8, XC>(i, o, g, co, zchunk, st)
+               : launch_fused_adv<TS, TC, 3, 32, d ? 2 : 4, XC>(i, o, g, co, zchunk, st);
+    case 3:
+      return b ? launch_fused_adv<TS, TC, 4, 32, d ? 2 : 4, XC>(i, o, g, co, zchunk, st)
+               : launch_fused_adv<TS, TC, 4, 32, d ? 1 : 2, XC>(i, o, g, co, zchunk, st);
   }
   return cudaErrorInvalidValue;
+}
+
+// tile = 2 * (loads of two x-pass items in flight) + (taller CTA)
+template <typename TS, typename TC>
+cudaError_t fused_dispatch(int m, int tile, const void *in, void *out, const Geom &g, const KronCoeffs<TC> &co,
+                           int zchunk, cudaStream_t st) {
+  const TS *i = static_cast<const TS *>(in);
+  TS *o = static_cast<TS *>(out);
+  const bool b = (tile & 1) != 0;
+  return tile >= 2 ? fused_dispatch_xc<TS, TC, 2>(m, b, i, o, g, co, zchunk, st)
+                   : fused_dispatch_xc<TS, TC, 1>(m, b, i, o, g, co, zchunk, st);
 }
 
 template <typename TS, typename TC>
 cudaError_t interp_dispatch(int m, const void *in, void *ws, const Geom &g, int z0, int nzl, const KronCoeffs<TC> &co,
                             cudaStream_t st) {
   const TS *i = static_cast<const TS *>(in);
+  constexpr bool d = sizeof(TC) == 8;
   Geom gs = g;
   gs.zlo = z0;
   gs.zhi = z0 + nzl;
@@ -266,7 +466,7 @@ cudaError_t interp_dispatch(int m, const void *in, void *ws, const Geom &g, int 
   switch (m) {
     case 1: return launch_kron<TS, TC, 2, 4, 32, 4, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
     case 2: return launch_kron<TS, TC, 3, 6, 32, 2, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
-    case 3: return launch_kron<TS, TC, 4, 8, 32, 1, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
+    case 3: return launch_kron<TS, TC, 4, 8, d ? 16 : 32, 1, 256, true>(i, ws, gs, co, zc, z0, nzl, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -286,11 +486,11 @@ cudaError_t evolve_dispatch(int m, const void *ws, void *out, const Geom &g, int
 
 }  // namespace
 
-cudaError_t launch_adv_fused(int m, int state, int compute, const void *in, void *out, const Geom &g,
+cudaError_t launch_adv_fused(int m, int tile, int state, int compute, const void *in, void *out, const Geom &g,
                              const KronCoeffs<double> &cd, const KronCoeffs<float> &cf, int zchunk, cudaStream_t st) {
-  if (compute == kF64) return fused_dispatch<double, double>(m, in, out, g, cd, zchunk, st);
-  if (state == kF64) return fused_dispatch<double, float>(m, in, out, g, cf, zchunk, st);
-  return fused_dispatch<float, float>(m, in, out, g, cf, zchunk, st);
+  if (compute == kF64) return fused_dispatch<double, double>(m, tile, in, out, g, cd, zchunk, st);
+  if (state == kF64) return fused_dispatch<double, float>(m, tile, in, out, g, cf, zchunk, st);
+  return fused_dispatch<float, float>(m, tile, in, out, g, cf, zchunk, st);
 }
 
 cudaError_t launch_adv_interp(int m, int state, int compute, const void *in, void *ws, const Geom &g, int z0, int nzl,

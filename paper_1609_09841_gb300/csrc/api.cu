@@ -176,7 +176,7 @@ int run_adv_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaS
   const int state = p->state == HERMITE_STATE_FP64 ? kF64 : kF32;
   cudaError_t e;
   if (p->variant != HERMITE_SPLIT) {
-    e = launch_adv_fused(p->m, state, compute, in, out, g, p->adv_fused, p->adv_fused32, p->zchunk, st);
+    e = launch_adv_fused(p->m, p->tile, state, compute, in, out, g, p->adv_fused, p->adv_fused32, p->zchunk, st);
     return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "advection half-step launch");
   }
   const int P = 2 * p->m + 2;
@@ -485,7 +485,8 @@ int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double
   p->adv_ev.tau = tau;
   for (int k = 0; k < 3; ++k) p->adv_ev.ah[k] = a[k] / h[k];
   p->adv_ev.q = q;
-  p->tile = 0;
+  // fastest fused schedules measured at 150^3 on GB300 (hermite_set_schedule overrides)
+  p->tile = prec == HERMITE_FP64 ? 1 : (m == 3 ? 3 : 0);
   p->zchunk = 16;
   p->ws_limit = (size_t)1 << 30;
   *out = p;
@@ -512,7 +513,7 @@ size_t hermite_state_elems(hermite_plan_t p) { return p ? p->elems : 0; }
 
 int hermite_schedule_count(hermite_plan_t p) {
   if (!p || p->batch) return 0;
-  if (p->eq) return 1;
+  if (p->eq) return p->variant == HERMITE_SPLIT ? 1 : kAdvFusedTiles;
   if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
   return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
 }

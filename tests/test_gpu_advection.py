@@ -130,8 +130,8 @@ def test_host_buffers_equal_device_buffers(torch_cuda, variant, prec, state):
 
 
 def test_zchunk_and_degenerate_grids(torch_cuda):
-    """Every zchunk gives the same result; grids of one node per dimension and
-    a single CTA tile agree with the oracle."""
+    """Every schedule (CTA shape and zchunk) gives the same result; grids of
+    one node per dimension and a single CTA tile agree with the oracle."""
     torch = torch_cuda
     from paper_1609_09841_gb300 import AdvectionPlan
     m = 2
@@ -141,16 +141,17 @@ def test_zchunk_and_degenerate_grids(torch_cuda):
         plan = AdvectionPlan(m, n, h, VEL, dt)
         x = HI.advection_random_state(m, n, seed=11)
         xd = torch.from_numpy(x).cuda()
-        outs = []
-        for zc in (1, 2, 16):
-            plan.set_schedule(0, zc)
-            yd = torch.empty_like(xd)
-            plan.step(xd, yd, 1)
-            outs.append(yd.cpu().numpy())
         ref = adv.half_step(x, m, h, VEL, dt, 1)
-        for o in outs:
-            assert _relmax(o, ref) <= 1e-12, n
-        assert np.array_equal(outs[0], outs[2])
+        for tile in range(plan.schedule_count()):
+            outs = []
+            for zc in (1, 2, 16):
+                plan.set_schedule(tile, zc)
+                yd = torch.empty_like(xd)
+                plan.step(xd, yd, 1)
+                outs.append(yd.cpu().numpy())
+            for o in outs:
+                assert _relmax(o, ref) <= 1e-12, (n, tile)
+            assert np.array_equal(outs[0], outs[2])
 
 
 def test_many_steps_match_oracle_run(torch_cuda):
@@ -214,3 +215,26 @@ def test_plane_wave_convergence_on_gpu(torch_cuda, m, n0):
         exact = HI.plane_wave(m, (n,) * 3, h, phase=2 * pi * 0.75)
         errs.append(float(np.max(np.abs(a.cpu().numpy()[0, 0, 0] - exact[0, 0, 0]))))
     assert np.log2(errs[0] / errs[1]) >= 2 * m + 1 - 0.5, errs
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("prec,state", [("fp64", "fp64"), ("fp32", "fp32"), ("fp32", "fp64")])
+def test_every_fused_schedule_matches_oracle(torch_cuda, m, prec, state):
+    """Each compiled CTA shape of the fused kernel, on the ragged multi-tile
+    grids, against the oracle (FP64 1e-12, FP32 the forward-error bound)."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import AdvectionPlan
+    n, h, dt = _setup(m, 0.4)
+    plan = AdvectionPlan(m, n, h, VEL, dt, prec=prec, state=state)
+    x = HI.advection_random_state(m, n, seed=330 + m)
+    if prec == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x).cuda().to(plan.torch_dtype)
+    ref = adv.half_step(x, m, h, VEL, dt, 0)
+    bound = 1e-12 * np.max(np.abs(ref)) if prec == "fp64" else _fp32_bound(m, h, VEL, dt, adv.full_q(m), x)
+    for tile in range(plan.schedule_count()):
+        plan.set_schedule(tile, 5)
+        yd = torch.empty_like(xd)
+        plan.step(xd, yd, 0)
+        err = float(np.max(np.abs(yd.double().cpu().numpy() - ref)))
+        assert err <= bound, (tile, err, bound)
