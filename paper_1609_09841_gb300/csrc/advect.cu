@@ -352,61 +352,62 @@ cudaError_t launch_fused_adv(const TS *in, TS *out, const Geom &g, const KronCoe
 namespace {
 
 // Alg. 4 on the cell polynomials of a slab, CB cells per CTA, then the
-// truncation to orders <= m (Sec. 2).  Shared memory holds three P^3 x CB
-// arrays [j][cell]: Ru, the current and the next Horner iterate.
-template <typename TS, typename TC, int M, int CB, int NT>
-__global__ void __launch_bounds__(NT)
+// truncation to orders <= m (Sec. 2).  A thread owns one row (cell, jz, jy)
+// of P coefficients along x1 in registers (with the row of Ru), so the
+// x1-derivative of a stage uses its own registers; the x2- and x3-derivatives
+// read the neighbouring rows (jy + 1, jz + 1) from one shared-memory copy of
+// the iterate, [jz][jy][jx][cell].  NT = CB * P^2 threads.
+template <typename TS, typename TC, int M, int CB>
+__global__ void __launch_bounds__(CB * 4 * M * M)
     adv_evolve_kernel(const TC *__restrict__ ws, TS *__restrict__ out, Geom g, int z0, int nzl, TC tau, TC ah0,
                       TC ah1, TC ah2, int q) {
-  constexpr int P = 2 * M, P3 = P * P * P;
+  constexpr int P = 2 * M;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC *base = reinterpret_cast<TC *>(smem_raw);
-  TC *w = base + P3 * CB;
-  TC *w2 = w + P3 * CB;
+  TC *w = reinterpret_cast<TC *>(smem_raw);  // [jz][jy][jx][k]
   const size_t ncell = (size_t)nzl * g.ny * g.nx;
   const size_t N = (size_t)g.nx * g.ny * g.nz;
-  const size_t c0 = (size_t)blockIdx.x * CB;
-  for (int e = threadIdx.x; e < P3 * CB; e += NT) {
-    const int k = e % CB, j = e / CB;
-    const size_t c = c0 + k;
-    const TC v = c < ncell ? ws[(size_t)j * ncell + c] : TC(0);
-    base[e] = v;
-    w[e] = v;
+  const int k = threadIdx.x % CB;
+  const int row = threadIdx.x / CB;  // jz * P + jy
+  const int jy = row % P, jz = row / P;
+  const size_t c = (size_t)blockIdx.x * CB + k;
+  const bool live = c < ncell;
+  TC base[P], cur[P];
+#pragma unroll
+  for (int jx = 0; jx < P; ++jx) {
+    base[jx] = live ? ws[(size_t)(row * P + jx) * ncell + c] : TC(0);
+    cur[jx] = base[jx];
   }
-  __syncthreads();
   for (int stage = q; stage >= 1; --stage) {  // w <- Ru + (tau / k) L w
     const TC f = tau / (TC)stage;
     const TC f0 = f * ah0, f1 = f * ah1, f2 = f * ah2;
-    for (int e = threadIdx.x; e < P3 * CB; e += NT) {
-      const int k = e % CB, j = e / CB;
-      const int jx = j % P, jy = (j / P) % P, jz = j / (P * P);
-      TC d = TC(0);
-      if (jx + 1 < P) d = fma(f0 * (TC)(jx + 1), w[(j + 1) * CB + k], d);
-      if (jy + 1 < P) d = fma(f1 * (TC)(jy + 1), w[(j + P) * CB + k], d);
-      if (jz + 1 < P) d = fma(f2 * (TC)(jz + 1), w[(j + P * P) * CB + k], d);
-      w2[e] = base[e] + d;
+#pragma unroll
+    for (int jx = 0; jx < P; ++jx) w[(row * P + jx) * CB + k] = cur[jx];
+    __syncthreads();
+    TC nxt[P];
+#pragma unroll
+    for (int jx = 0; jx < P; ++jx) {
+      TC d = jx + 1 < P ? f0 * (TC)(jx + 1) * cur[jx + 1] : TC(0);
+      if (jy + 1 < P) d = fma(f1 * (TC)(jy + 1), w[((row + 1) * P + jx) * CB + k], d);
+      if (jz + 1 < P) d = fma(f2 * (TC)(jz + 1), w[((row + P) * P + jx) * CB + k], d);
+      nxt[jx] = base[jx] + d;
     }
     __syncthreads();
-    TC *t = w;
-    w = w2;
-    w2 = t;
+#pragma unroll
+    for (int jx = 0; jx < P; ++jx) cur[jx] = nxt[jx];
   }
-  for (int e = threadIdx.x; e < M * M * M * CB; e += NT) {
-    const int k = e % CB, i = e / CB;
-    const size_t c = c0 + k;
-    if (c >= ncell) continue;
-    const int i1 = i % M, i2 = (i / M) % M, i3 = i / (M * M);
-    out[(size_t)i * N + (size_t)z0 * g.ny * g.nx + c] = (TS)w[((i3 * P + i2) * P + i1) * CB + k];
-  }
+  if (!live || jy > M - 1 || jz > M - 1) return;
+#pragma unroll
+  for (int i1 = 0; i1 < M; ++i1)
+    out[(size_t)((jz * M + jy) * M + i1) * N + (size_t)z0 * g.ny * g.nx + c] = (TS)cur[i1];
 }
 
-template <typename TS, typename TC, int M, int CB, int NT>
+template <typename TS, typename TC, int M, int CB>
 cudaError_t launch_evolve_adv(const TC *ws, TS *out, const Geom &g, int z0, int nzl, const AdvEvolveParams &ep,
                               cudaStream_t st) {
-  constexpr int P = 2 * M;
-  constexpr size_t smem = (size_t)3 * P * P * P * CB * sizeof(TC);
-  static_assert(smem <= 227 * 1024, "shared memory of the evolution kernel");
-  auto kern = adv_evolve_kernel<TS, TC, M, CB, NT>;
+  constexpr int P = 2 * M, NT = CB * P * P;
+  static_assert(NT <= 1024, "threads per CTA");
+  constexpr size_t smem = (size_t)P * P * P * CB * sizeof(TC);
+  auto kern = adv_evolve_kernel<TS, TC, M, CB>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -477,9 +478,9 @@ cudaError_t evolve_dispatch(int m, const void *ws, void *out, const Geom &g, int
   const TC *w = static_cast<const TC *>(ws);
   TS *o = static_cast<TS *>(out);
   switch (m) {
-    case 1: return launch_evolve_adv<TS, TC, 2, 32, 256>(w, o, g, z0, nzl, ep, st);
-    case 2: return launch_evolve_adv<TS, TC, 3, 16, 256>(w, o, g, z0, nzl, ep, st);
-    case 3: return launch_evolve_adv<TS, TC, 4, 8, 256>(w, o, g, z0, nzl, ep, st);
+    case 1: return launch_evolve_adv<TS, TC, 2, 32>(w, o, g, z0, nzl, ep, st);
+    case 2: return launch_evolve_adv<TS, TC, 3, 16>(w, o, g, z0, nzl, ep, st);
+    case 3: return launch_evolve_adv<TS, TC, 4, 16>(w, o, g, z0, nzl, ep, st);
   }
   return cudaErrorInvalidValue;
 }
