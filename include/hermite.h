@@ -64,7 +64,8 @@ enum hermite_status {
   HERMITE_EUNSUPPORTED = -4, /* combination of precision / state type / variant not provided */
   HERMITE_EUNSTABLE = -5,    /* c*(dt/2)/h_k above the stability limit of order m */
   HERMITE_ETIMEOUT = -6,     /* a bounded device-side wait gave up (batched scheduler) */
-  HERMITE_ENONFINITE = -7    /* hermite_error saw a NaN or Inf */
+  HERMITE_ENONFINITE = -7,   /* hermite_error saw a NaN or Inf */
+  HERMITE_ENOCONV = -8       /* the eigenvalue iteration of a symbol did not converge */
 };
 
 /* Arithmetic of the contractions (interpolation and evolution). */
@@ -277,8 +278,48 @@ double hermite_stability_limit(int m);
 
 /* The same for q Taylor stages (4..3(2m+1)); 0 outside that range.  Not
  * monotone in q: m = 3 with q = 5 is stable only up to 0.09, while the full
- * series reaches 0.47 / 0.42 / 0.40 for m = 1 / 2 / 3. */
+ * series reaches 0.47 / 0.42 / 0.37 for m = 1 / 2 / 3 (at m = 3 the first
+ * instability, 0.373, lies below a stable band around 0.40). */
 double hermite_stability_limit_taylor(int m, int q);
+
+/* ---- Stability tool (Sec. 2's stability condition, computed) ------------
+ * The spectral radius of the Fourier symbol of one half step, and the
+ * largest stable time step for a given order, series length and grid.  For
+ * a mode exp(i theta . x / h) the symbol is the 2(m+1)^3 (wave) or (m+1)^3
+ * (advection) square complex matrix of the half step; the scheme is stable
+ * when its spectral radius is at most one for every theta.  Host-only
+ * computations (no GPU, no plan needed): the wave symbol is assembled from
+ * the same 1-D tables the kernels use, the advection symbol from the cell
+ * matrix of interpolation + Alg. 4 + truncation; eigenvalues by a Hessenberg
+ * reduction and the shifted QR iteration.
+ *
+ * hermite_symbol_radius: rho(G(theta)) of the wave half step with q Taylor
+ *   stages (4..3(2m+1)), speed c, spacings h, full step dt.
+ * hermite_max_radius: max rho over an npts^3 grid of theta in [0, pi]^3
+ *   (the symbol at -theta is the conjugate), 1 <= npts <= 64.
+ * hermite_max_dt: the largest dt such that max rho <= 1 + 1e-10 at every
+ *   step up to it, for the given (possibly anisotropic) h and 2 <= npts <= 64.
+ *   The stable steps need not form an interval (m = 3 with the whole series
+ *   is weakly unstable for c tau / h in about (0.373, 0.39) and stable again
+ *   at 0.40), so the steps 1.2 h_min k / (60 c), k = 1, 2, ..., are scanned
+ *   to the first unstable one, whose bracket is then bisected to 1e-4
+ *   relative; a window of instability narrower than the scan step can be
+ *   missed.  hermite_plan's tables are this bound for h1 = h2 = h3 on a finer
+ *   scan, rounded down.  Runs on up to 16 host threads; about a minute for
+ *   m = 3 at npts = 7.
+ * hermite_adv_symbol_radius / hermite_adv_max_dt: the same for advection
+ *   with velocity a (q = 0: the whole series); a = 0 is EINVAL for the bound.
+ * Errors: EINVAL for arguments out of range, ENOCONV if an eigenvalue
+ * iteration did not converge. */
+int hermite_symbol_radius(int m, int q, double c, const double h[3], double dt, const double theta[3],
+                          double *rho);
+int hermite_max_dt(int m, int q, double c, const double h[3], int npts, double *dt);
+int hermite_max_radius(int m, int q, double c, const double h[3], double dt, int npts, double *rho);
+int hermite_adv_symbol_radius(int m, int q, const double a[3], const double h[3], double dt,
+                              const double theta[3], double *rho);
+int hermite_adv_max_dt(int m, int q, const double a[3], const double h[3], int npts, double *dt);
+int hermite_adv_max_radius(int m, int q, const double a[3], const double h[3], double dt, int npts,
+                           double *rho);
 
 /* Copy the plan's 1-D interpolation operator H (P x P, row-major, H[j][(side,i)]:
  * monomial coefficient j from [left i = 0..m, right i = 0..m], Sec. 3.1) to

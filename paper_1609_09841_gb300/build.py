@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhermite.so")
-SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu", "advect.cu"]
+SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu", "advect.cu", "symbol.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + \
     os.environ.get("HERMITE_NVCC_FLAGS", "").split()
@@ -60,7 +60,7 @@ def build(verbose=False, force=False):
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath=/usr/local/cuda/lib64",
-                                  "-o", LIB] + objs
+                                  "-o", LIB] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -17,6 +17,7 @@ HERMITE_EUNSUPPORTED = -4
 HERMITE_EUNSTABLE = -5
 HERMITE_ETIMEOUT = -6
 HERMITE_ENONFINITE = -7
+HERMITE_ENOCONV = -8
 
 HERMITE_FP64 = 0
 HERMITE_FP32 = 1
@@ -29,7 +30,7 @@ HERMITE_FUSED = 1
 HERMITE_SPLIT = 2
 
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EUNSUPPORTED",
-                -5: "EUNSTABLE", -6: "ETIMEOUT", -7: "ENONFINITE"}
+                -5: "EUNSTABLE", -6: "ETIMEOUT", -7: "ENONFINITE", -8: "ENOCONV"}
 
 
 class HermiteError(RuntimeError):
@@ -55,6 +56,12 @@ def _load():
         "hermite_stability_limit_taylor": (D, [I, I]),
         "hermite_adv_plan": (I, [ctypes.POINTER(P), I, IP, DP, DP, D, I, I, I, I]),
         "hermite_adv_stability_limit": (D, [I, I]),
+        "hermite_symbol_radius": (I, [I, I, D, DP, D, DP, DP]),
+        "hermite_max_dt": (I, [I, I, D, DP, I, DP]),
+        "hermite_max_radius": (I, [I, I, D, DP, D, I, DP]),
+        "hermite_adv_max_radius": (I, [I, I, DP, DP, D, I, DP]),
+        "hermite_adv_symbol_radius": (I, [I, I, DP, DP, D, DP, DP]),
+        "hermite_adv_max_dt": (I, [I, I, DP, DP, I, DP]),
         "hermite_plan_operator": (I, [P, DP]),
         "hermite_destroy": (None, [P]),
         "hermite_step_dc": (I, [P, P, P, I, P]),

@@ -18,10 +18,11 @@
 // reads the node pairs straight from global memory (coalesced along x1, the
 // right neighbour of one thread is the left of the next, an L1 hit; each
 // thread issues all its loads of the plane before any arithmetic), writes
-// its results to shared memory; the y-pass turns them into face results,
-// kept for two planes (double buffer); the z-pass combines the face results
-// of planes p-1 and p.  Two barriers per plane.  Every per-item index is
-// computed once before the march.
+// its results to shared memory; the y-pass turns them into face results
+// (one plane in shared memory); the z-pass adds each plane's share to the
+// cell below it (completed and stored) and the cell above it (kept in
+// registers until the next plane).  Two barriers per plane.  Every per-item
+// index is computed once before the march.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,7 +40,7 @@ struct FusedShape {
   static constexpr int NG = (2 * (NA - 1) < G ? 2 * (NA - 1) : G) + 1;  // grades of the y-pass results
   static constexpr int SX = 2 * M * M * NA * M * NYN * TX;  // x-pass results [f][iz][iy][a][ix'][ey][ex]
   static constexpr int SY = 2 * NG * M * M * M * TX * TY;   // y-pass results [f][g][iz][iy'][ix'][fy][fx]
-  static constexpr size_t SMEM = (size_t)(SX + 2 * SY) * sizeof(TC);  // sY double-buffered by plane
+  static constexpr size_t SMEM = (size_t)(SX + SY) * sizeof(TC);  // one plane of y-pass results
   static constexpr int XITEMS = 2 * M * M * NYN * TX;       // (f, iz, iy, edge)
   static constexpr int YITEMS = 2 * M * M * TY * TX;        // (f, iz, ix', face)
   static constexpr int ZITEMS = M * M * TX * TY;            // (iy', ix', cell)
@@ -51,7 +52,7 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 }
 
 // One tile: output nodes [x0, x0+TX) x [y0, y0+TY) x [z0, z1) of one grid.
-// sX, sY: shared memory of FusedShape<TC, M, TX, TY>::SX and 2 * ::SY elements.
+// sX, sY: shared memory of FusedShape<TC, M, TX, TY>::SX and ::SY elements.
 // All NT threads of the CTA must call it; it starts and ends without a
 // pending barrier (callers that reuse sX, sY or `co` for another tile must
 // put a __syncthreads() between the calls).
@@ -118,6 +119,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     zxy[k] = (e < Sh::ZITEMS && ox < nx && oy < ny) ? oy * nx + ox : -1;
   }
 
+  TC zacc[ZPT][2][M];  // pending cell of each z-item: [f_out][r]
   for (int p = 0; p <= z1 - z0; ++p) {
     const size_t zoff = (size_t)wrap_index(z0 + s + p, nz) * pxy;
     // x-pass on the TX x (TY+1) x-edges of node plane z0 + s + p
@@ -154,99 +156,128 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         }
     }
     __syncthreads();
-    // y-pass on the TX x TY xy-faces
+    // y-pass on the TX x TY xy-faces, accumulated grade by grade
 #pragma unroll
     for (int k = 0; k < YPT; ++k) {
       if (ydst[k] < 0) continue;
-      TC sv[NA][M], dv[NA][M];
+      TC acc[NG][M];
+#pragma unroll
+      for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int r = 0; r < M; ++r) acc[gg][r] = TC(0);
 #pragma unroll
       for (int a = 0; a < NA; ++a)
 #pragma unroll
         for (int iy = 0; iy < M; ++iy) {
           const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
           const TC L = xi[0], R = xi[TX];
-          sv[a][iy] = (iy & 1) ? R - L : R + L;
-          dv[a][iy] = (iy & 1) ? R + L : R - L;
-        }
-      TC *yo = sY + (p & 1) * Sh::SY + ydst[k];
+          const TC sv = (iy & 1) ? R - L : R + L;
+          const TC dv = (iy & 1) ? R + L : R - L;
 #pragma unroll
-      for (int gg = 0; gg < NG; ++gg)
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          TC acc = 0;
-#pragma unroll
-          for (int a = 0; a < NA; ++a) {
+          for (int gg = 0; gg < NG; ++gg) {
             const int b = gg - a;
             if (b < 0 || b >= NA) continue;
 #pragma unroll
-            for (int i = 0; i < M; ++i) acc = fma(co.gy[b][r * 4 + i], (r & 1) ? dv[a][i] : sv[a][i], acc);
+            for (int r = 0; r < M; ++r) acc[gg][r] = fma(co.gy[b][r * 4 + iy], (r & 1) ? dv : sv, acc[gg][r]);
           }
-          yo[(gg * M * M * M + r * M) * YS] = acc;
         }
+      TC *yo = sY + ydst[k];
+#pragma unroll
+      for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int r = 0; r < M; ++r) yo[(gg * M * M * M + r * M) * YS] = acc[gg][r];
     }
     __syncthreads();
-    // z-pass: cell layer z0 + p - 1 from the faces of planes p - 1 and p
-    // (the two halves of sY).  The next plane's x-pass writes sX, last read
-    // by this plane's y-pass before the barrier above; its y-pass overwrites
-    // the half of sY read here only after the next barrier.
-    if (p > 0) {
-      const TC *yc = sY + (p & 1) * Sh::SY, *yp = sY + ((p - 1) & 1) * Sh::SY;
+    // z-pass.  Plane p is the upper face of cell z0 + p - 1 and the lower face
+    // of cell z0 + p.  With E_r, O_r the sums over even and odd iz of
+    // Kz[r][iz] Y_iz, the reflection symmetry G[r][(lower, iz)] =
+    // (-1)^(r+iz) G[r][(upper, iz)] makes the plane's share of the cell below
+    // E_r + O_r and of the cell above (-1)^r (E_r - O_r): the first completes
+    // the pending cell, the second starts the next one (kept in registers).
+    // The next plane's y-pass overwrites sY only after its x-pass barrier.
 #pragma unroll
-      for (int k = 0; k < ZPT; ++k) {
-        if (zxy[k] < 0) continue;
-        TC sv[2][NG][M], dv[2][NG][M];
+    for (int k = 0; k < ZPT; ++k) {
+      if (zxy[k] < 0) continue;
+      TC E[2][M], O[2][M];
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
+      for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
-          for (int gg = 0; gg < NG; ++gg)
+        for (int r = 0; r < M; ++r) E[fo][r] = O[fo][r] = TC(0);
 #pragma unroll
-            for (int iz = 0; iz < M; ++iz) {
-              const int q = zsrc[k] + ((f * NG + gg) * M + iz) * M * M * YS;
-              const TC L = yp[q], R = yc[q];
-              sv[f][gg][iz] = (iz & 1) ? R - L : R + L;
-              dv[f][gg][iz] = (iz & 1) ? R + L : R - L;
-            }
+      for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+          for (int iz = 0; iz < M; ++iz) {
+            const TC y = sY[zsrc[k] + ((fi * NG + gg) * M + iz) * M * M * YS];
+#pragma unroll
+            for (int fo = 0; fo < 2; ++fo)
+#pragma unroll
+              for (int r = 0; r < M; ++r) {
+                const TC w = co.kz[fo][fi][gg][r * 4 + iz];
+                if (iz & 1)
+                  O[fo][r] = fma(w, y, O[fo][r]);
+                else
+                  E[fo][r] = fma(w, y, E[fo][r]);
+              }
+          }
+      if (p > 0) {
         TS *o = out + (size_t)(z0 + p - 1) * pxy + zxy[k] + (size_t)zcomp[k] * plane;
 #pragma unroll
         for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
-          for (int r = 0; r < M; ++r) {
-            TC acc = 0;
-#pragma unroll
-            for (int fi = 0; fi < 2; ++fi)
-#pragma unroll
-              for (int gg = 0; gg < NG; ++gg)
-#pragma unroll
-                for (int i = 0; i < M; ++i)
-                  acc = fma(co.kz[fo][fi][gg][r * 4 + i], (r & 1) ? dv[fi][gg][i] : sv[fi][gg][i], acc);
-            o[(size_t)((fo * M + r) * M * M) * plane] = (TS)acc;
-          }
+          for (int r = 0; r < M; ++r) o[(size_t)((fo * M + r) * M * M) * plane] = (TS)(zacc[k][fo][r] + (E[fo][r] + O[fo][r]));
       }
+#pragma unroll
+      for (int fo = 0; fo < 2; ++fo)
+#pragma unroll
+        for (int r = 0; r < M; ++r) zacc[k][fo][r] = (r & 1) ? O[fo][r] - E[fo][r] : E[fo][r] - O[fo][r];
     }
   }
 }
+
+#define HERMITE_FUSED_KERNEL_BODY                                                                   \
+  using Sh = FusedShape<TC, M, TX, TY, G>;                                                          \
+  extern __shared__ __align__(16) unsigned char smem_raw[];                                        \
+  TC *sX = reinterpret_cast<TC *>(smem_raw);                                                       \
+  TC *sY = sX + Sh::SX;                                                                            \
+  const int tiles_x = (g.nx + TX - 1) / TX;                                                        \
+  const int x0 = (blockIdx.x % tiles_x) * TX;                                                      \
+  const int y0 = (blockIdx.x / tiles_x) * TY;                                                      \
+  const int z0 = g.zlo + blockIdx.y * zchunk;                                                      \
+  if (z0 >= g.zhi) return;                                                                         \
+  fused_tile<TS, TC, M, TX, TY, NT, G>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
 
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
 __global__ void __launch_bounds__(NT)
     fused_step_kernel(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
                       const StepCoeffs<TC> co) {
-  using Sh = FusedShape<TC, M, TX, TY, G>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TC *sX = reinterpret_cast<TC *>(smem_raw);
-  TC *sY = sX + Sh::SX;
-  const int tiles_x = (g.nx + TX - 1) / TX;
-  const int x0 = (blockIdx.x % tiles_x) * TX;
-  const int y0 = (blockIdx.x / tiles_x) * TY;
-  const int z0 = g.zlo + blockIdx.y * zchunk;
-  if (z0 >= g.zhi) return;
-  fused_tile<TS, TC, M, TX, TY, NT, G>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
+  HERMITE_FUSED_KERNEL_BODY
 }
 
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
+// The same kernel with a register cap that lets MINB CTAs share an SM
+// (spilling if needed).  Without a second __launch_bounds__ argument ptxas
+// allocates fewer registers than with an explicit 1, so the plain kernel
+// above is kept for MINB = 1.
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    fused_step_kernel_mb(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
+                         const StepCoeffs<TC> co) {
+  HERMITE_FUSED_KERNEL_BODY
+}
+
+#undef HERMITE_FUSED_KERNEL_BODY
+
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, int MINB = 1>
 cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoeffs<TC> &co,
                              int zchunk, cudaStream_t st) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
-  auto kern = fused_step_kernel<TS, TC, M, TX, TY, NT, G>;
+  auto kern = [] {
+    if constexpr (MINB > 1)
+      return fused_step_kernel_mb<TS, TC, M, TX, TY, NT, G, MINB>;
+    else
+      return fused_step_kernel<TS, TC, M, TX, TY, NT, G>;
+  }();
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);

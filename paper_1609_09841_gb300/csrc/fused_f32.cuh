@@ -13,14 +13,20 @@ cudaError_t dispatch_f32(int m, int tile, const TS *in, TS *out, const Geom &g, 
     case 8 + 1: return launch_fused_cfg<TS, float, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
     case 8 + 2: return launch_fused_cfg<TS, float, 2, 32, 4, 512>(in, out, g, co, zchunk, st);
     case 8 + 3: return launch_fused_cfg<TS, float, 2, 16, 16, 1024>(in, out, g, co, zchunk, st);
+    case 8 + 4: return launch_fused_cfg<TS, float, 2, 8, 8, 256, 2, 4>(in, out, g, co, zchunk, st);
+    case 8 + 5: return launch_fused_cfg<TS, float, 2, 32, 4, 512, 2, 2>(in, out, g, co, zchunk, st);
     case 16 + 0: return launch_fused_cfg<TS, float, 3, 8, 4, 288>(in, out, g, co, zchunk, st);
     case 16 + 1: return launch_fused_cfg<TS, float, 3, 4, 4, 160>(in, out, g, co, zchunk, st);
     case 16 + 2: return launch_fused_cfg<TS, float, 3, 8, 8, 576>(in, out, g, co, zchunk, st);
     case 16 + 3: return launch_fused_cfg<TS, float, 3, 16, 4, 576>(in, out, g, co, zchunk, st);
+    case 16 + 4: return launch_fused_cfg<TS, float, 3, 8, 4, 288, 2, 3>(in, out, g, co, zchunk, st);
+    case 16 + 5: return launch_fused_cfg<TS, float, 3, 4, 4, 160, 2, 5>(in, out, g, co, zchunk, st);
     case 24 + 0: return launch_fused_cfg<TS, float, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
     case 24 + 1: return launch_fused_cfg<TS, float, 4, 8, 4, 256>(in, out, g, co, zchunk, st);
     case 24 + 2: return launch_fused_cfg<TS, float, 4, 8, 4, 512>(in, out, g, co, zchunk, st);
     case 24 + 3: return launch_fused_cfg<TS, float, 4, 4, 4, 128>(in, out, g, co, zchunk, st);
+    case 24 + 4: return launch_fused_cfg<TS, float, 4, 4, 4, 256, 2, 3>(in, out, g, co, zchunk, st);
+    case 24 + 5: return launch_fused_cfg<TS, float, 4, 8, 2, 256, 2, 3>(in, out, g, co, zchunk, st);
   }
   return cudaErrorInvalidValue;
 }

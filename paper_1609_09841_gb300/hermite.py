@@ -202,3 +202,55 @@ class AdvectionPlan(Plan):
         """(max_abs, max_rel, rms, l2_rel) of x - ref (one field; mask bit 4:
         every derivative component, else values only)."""
         return super().error(x, ref, mask, stream)
+
+
+def _d3(v):
+    return (ctypes.c_double * 3)(*[float(x) for x in v])
+
+
+def symbol_radius(m, h, c, dt, theta, q=4):
+    """Spectral radius of the Fourier symbol of the wave half step at theta."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_symbol_radius(int(m), int(q), float(c), _d3(h), float(dt), _d3(theta),
+                                              ctypes.byref(out)))
+    return out.value
+
+
+def max_dt(m, h, c, q=4, npts=7):
+    """Largest stable full step dt of the wave half step for spacings h (the
+    symbol's spectral radius <= 1 on an npts^3 grid of theta)."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_max_dt(int(m), int(q), float(c), _d3(h), int(npts), ctypes.byref(out)))
+    return out.value
+
+
+def adv_symbol_radius(m, h, a, dt, theta, q=0):
+    """Spectral radius of the Fourier symbol of the advection half step."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_adv_symbol_radius(int(m), int(q), _d3(a), _d3(h), float(dt), _d3(theta),
+                                                  ctypes.byref(out)))
+    return out.value
+
+
+def adv_max_dt(m, h, a, q=0, npts=7):
+    """Largest stable full step dt of the advection half step."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_adv_max_dt(int(m), int(q), _d3(a), _d3(h), int(npts), ctypes.byref(out)))
+    return out.value
+
+
+def max_radius(m, h, c, dt, q=4, npts=7):
+    """Largest spectral radius of the wave half step's symbol on an npts^3
+    grid of theta."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_max_radius(int(m), int(q), float(c), _d3(h), float(dt), int(npts),
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def adv_max_radius(m, h, a, dt, q=0, npts=7):
+    """Largest spectral radius of the advection half step's symbol."""
+    out = ctypes.c_double()
+    capi.check(capi.lib.hermite_adv_max_radius(int(m), int(q), _d3(a), _d3(h), float(dt), int(npts),
+                                               ctypes.byref(out)))
+    return out.value
