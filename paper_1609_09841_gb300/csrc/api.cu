@@ -151,7 +151,9 @@ int ensure_red(hermite_plan_s *p) {
 // Advection (Eq. 1 with a constant velocity a): largest max_k |a_k| tau / h_k
 // per order m and Taylor order q, the smaller of the limits of the Fourier
 // symbol for a mode along x1 (a along x1) and for the diagonal (a = (1, 1, 1)
-// direction, 7^3 theta grid), rounded down to two decimals.  With the whole
+// direction, 7^3 theta grid), rounded down to two decimals; every entry is at
+// or below the first instability found by hermite_adv_max_radius on a 0.0025
+// scan (no unstable window lies below an entry).  With the whole
 // series (q = 3(2m+1)) the half step is a Kronecker product of 1-D maps and the
 // limit is the half cell of Sec. 2; q = 1 (forward Euler) has no stable step.
 const double kAdvLimit[4][kMaxQ + 1] = {
