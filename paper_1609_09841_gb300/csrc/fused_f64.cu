@@ -8,7 +8,7 @@ namespace hermite {
 
 int fused_tile_count(int prec, int m) {
   (void)m;
-  return prec == 0 ? 3 : 6;
+  return prec == 0 ? 5 : 6;
 }
 
 cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,
@@ -18,12 +18,18 @@ cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, con
     case 8 + 0: return launch_fused_cfg<T, T, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
     case 8 + 1: return launch_fused_cfg<T, T, 2, 16, 4, 256>(in, out, g, co, zchunk, st);
     case 8 + 2: return launch_fused_cfg<T, T, 2, 16, 8, 512>(in, out, g, co, zchunk, st);
+    case 8 + 3: return launch_fused_cfg<T, T, 2, 8, 8, 256, 2, 2>(in, out, g, co, zchunk, st);
+    case 8 + 4: return launch_fused_cfg<T, T, 2, 16, 4, 256, 2, 2>(in, out, g, co, zchunk, st);
     case 16 + 0: return launch_fused_cfg<T, T, 3, 4, 4, 160>(in, out, g, co, zchunk, st);
     case 16 + 1: return launch_fused_cfg<T, T, 3, 8, 4, 288>(in, out, g, co, zchunk, st);
     case 16 + 2: return launch_fused_cfg<T, T, 3, 4, 8, 288>(in, out, g, co, zchunk, st);
+    case 16 + 3: return launch_fused_cfg<T, T, 3, 4, 4, 160, 2, 3>(in, out, g, co, zchunk, st);
+    case 16 + 4: return launch_fused_cfg<T, T, 3, 8, 4, 288, 2, 2>(in, out, g, co, zchunk, st);
     case 24 + 0: return launch_fused_cfg<T, T, 4, 4, 4, 256>(in, out, g, co, zchunk, st);
     case 24 + 1: return launch_fused_cfg<T, T, 4, 4, 2, 128>(in, out, g, co, zchunk, st);
     case 24 + 2: return launch_fused_cfg<T, T, 4, 8, 2, 256>(in, out, g, co, zchunk, st);
+    case 24 + 3: return launch_fused_cfg<T, T, 4, 4, 4, 256, 2, 2>(in, out, g, co, zchunk, st);
+    case 24 + 4: return launch_fused_cfg<T, T, 4, 4, 2, 128, 2, 3>(in, out, g, co, zchunk, st);
   }
   return cudaErrorInvalidValue;
 }
