@@ -27,6 +27,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+#include <type_traits>
+
 #include "hermite_impl.h"
 
 namespace hermite {
@@ -46,6 +49,54 @@ struct FusedShape {
   static constexpr int ZITEMS = M * M * TX * TY;            // (iy', ix', cell)
 };
 
+// Packed FP32 pairs for fma.rn.f32x2 (two lane-wise fma.rn.f32 in one
+// instruction, same rounding as two scalar FMAs).  In the FP32 kernels the
+// passes pair outputs that share their input: rows (r, r+1) of the x- and
+// y-pass factors act on the butterfly pair (sum, difference), and the two
+// output fields of the z-pass act on the same y-pass value.
+struct PackedCoeffs {
+  unsigned long long gx[kMaxA][2][4];     // (gx[a][(2rp)*4+i], gx[a][(2rp+1)*4+i])
+  unsigned long long gy[kMaxA][2][4];     // the same for gy
+  unsigned long long kz[2][kMaxG][4][4];  // [f_in][g][r][iz]: (kz[0][f_in][g][r*4+iz], kz[1][f_in][g][r*4+iz])
+};
+
+inline unsigned long long pack_pair_host(float lo, float hi) {
+  unsigned a, b;
+  std::memcpy(&a, &lo, 4);
+  std::memcpy(&b, &hi, 4);
+  return ((unsigned long long)b << 32) | a;
+}
+
+inline PackedCoeffs pack_coeffs(const StepCoeffs<float> &c) {
+  PackedCoeffs p{};
+  for (int a = 0; a < kMaxA; ++a)
+    for (int rp = 0; rp < 2; ++rp)
+      for (int i = 0; i < 4; ++i) {
+        p.gx[a][rp][i] = pack_pair_host(c.gx[a][(2 * rp) * 4 + i], c.gx[a][(2 * rp + 1) * 4 + i]);
+        p.gy[a][rp][i] = pack_pair_host(c.gy[a][(2 * rp) * 4 + i], c.gy[a][(2 * rp + 1) * 4 + i]);
+      }
+  for (int fi = 0; fi < 2; ++fi)
+    for (int g = 0; g < kMaxG; ++g)
+      for (int r = 0; r < 4; ++r)
+        for (int iz = 0; iz < 4; ++iz)
+          p.kz[fi][g][r][iz] = pack_pair_host(c.kz[0][fi][g][r * 4 + iz], c.kz[1][fi][g][r * 4 + iz]);
+  return p;
+}
+
+__device__ __forceinline__ unsigned long long pack2f(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2f(unsigned long long v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2f(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ int wrap_index(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -56,10 +107,13 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // All NT threads of the CTA must call it; it starts and ends without a
 // pending barrier (callers that reuse sX, sY or `co` for another tile must
 // put a __syncthreads() between the calls).
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
+// PK: FP32 passes with fma.rn.f32x2 on the packed tables `pc` (kernel
+// parameters); bitwise the same results as the scalar FMAs.
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
-                                           TC *__restrict__ sX, TC *__restrict__ sY) {
+                                           TC *__restrict__ sX, TC *__restrict__ sY,
+                                           const PackedCoeffs *pc = nullptr) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
   constexpr int NYN = Sh::NYN, NA = Sh::NA, NG = Sh::NG;
   constexpr int XPT = (Sh::XITEMS + NT - 1) / NT;
@@ -145,47 +199,112 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         dv[i] = (i & 1) ? R + L : R - L;
       }
       TC *xo = sX + xdst[k];
+      if constexpr (PK) {
+        unsigned long long sd[M];
 #pragma unroll
-      for (int a = 0; a < NA; ++a)
+        for (int i = 0; i < M; ++i) sd[i] = pack2f(sv[i], dv[i]);
 #pragma unroll
-        for (int r = 0; r < M; ++r) {
-          TC acc = 0;
+        for (int a = 0; a < NA; ++a) {
 #pragma unroll
-          for (int i = 0; i < M; ++i) acc = fma(co.gx[a][r * 4 + i], (r & 1) ? dv[i] : sv[i], acc);
-          xo[(a * M + r) * XS] = acc;
+          for (int rp = 0; rp < M / 2; ++rp) {
+            unsigned long long acc = 0ull;
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc = fma2f(pc->gx[a][rp][i], sd[i], acc);
+            float lo, hi;
+            unpack2f(acc, lo, hi);
+            xo[(a * M + 2 * rp) * XS] = lo;
+            xo[(a * M + 2 * rp + 1) * XS] = hi;
+          }
+          if constexpr (M & 1) {
+            TC acc = 0;
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc = fma(co.gx[a][(M - 1) * 4 + i], sv[i], acc);
+            xo[(a * M + M - 1) * XS] = acc;
+          }
         }
+      } else {
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+          for (int r = 0; r < M; ++r) {
+            TC acc = 0;
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc = fma(co.gx[a][r * 4 + i], (r & 1) ? dv[i] : sv[i], acc);
+            xo[(a * M + r) * XS] = acc;
+          }
+      }
     }
     __syncthreads();
     // y-pass on the TX x TY xy-faces, accumulated grade by grade
 #pragma unroll
     for (int k = 0; k < YPT; ++k) {
       if (ydst[k] < 0) continue;
-      TC acc[NG][M];
-#pragma unroll
-      for (int gg = 0; gg < NG; ++gg)
-#pragma unroll
-        for (int r = 0; r < M; ++r) acc[gg][r] = TC(0);
-#pragma unroll
-      for (int a = 0; a < NA; ++a)
-#pragma unroll
-        for (int iy = 0; iy < M; ++iy) {
-          const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
-          const TC L = xi[0], R = xi[TX];
-          const TC sv = (iy & 1) ? R - L : R + L;
-          const TC dv = (iy & 1) ? R + L : R - L;
-#pragma unroll
-          for (int gg = 0; gg < NG; ++gg) {
-            const int b = gg - a;
-            if (b < 0 || b >= NA) continue;
-#pragma unroll
-            for (int r = 0; r < M; ++r) acc[gg][r] = fma(co.gy[b][r * 4 + iy], (r & 1) ? dv : sv, acc[gg][r]);
-          }
-        }
       TC *yo = sY + ydst[k];
+      if constexpr (PK) {
+        unsigned long long acc2[NG][M / 2 > 0 ? M / 2 : 1];
+        TC accr[NG];  // row M - 1 when M is odd
 #pragma unroll
-      for (int gg = 0; gg < NG; ++gg)
+        for (int gg = 0; gg < NG; ++gg) {
 #pragma unroll
-        for (int r = 0; r < M; ++r) yo[(gg * M * M * M + r * M) * YS] = acc[gg][r];
+          for (int rp = 0; rp < M / 2; ++rp) acc2[gg][rp] = 0ull;
+          accr[gg] = TC(0);
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+          for (int iy = 0; iy < M; ++iy) {
+            const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
+            const TC L = xi[0], R = xi[TX];
+            const TC sv = (iy & 1) ? R - L : R + L;
+            const TC dv = (iy & 1) ? R + L : R - L;
+            const unsigned long long sd = pack2f(sv, dv);
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) {
+              const int b = gg - a;
+              if (b < 0 || b >= NA) continue;
+#pragma unroll
+              for (int rp = 0; rp < M / 2; ++rp) acc2[gg][rp] = fma2f(pc->gy[b][rp][iy], sd, acc2[gg][rp]);
+              if constexpr (M & 1) accr[gg] = fma(co.gy[b][(M - 1) * 4 + iy], sv, accr[gg]);
+            }
+          }
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+#pragma unroll
+          for (int rp = 0; rp < M / 2; ++rp) {
+            float lo, hi;
+            unpack2f(acc2[gg][rp], lo, hi);
+            yo[(gg * M * M * M + 2 * rp * M) * YS] = lo;
+            yo[(gg * M * M * M + (2 * rp + 1) * M) * YS] = hi;
+          }
+          if constexpr (M & 1) yo[(gg * M * M * M + (M - 1) * M) * YS] = accr[gg];
+        }
+      } else {
+        TC acc[NG][M];
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+          for (int r = 0; r < M; ++r) acc[gg][r] = TC(0);
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+#pragma unroll
+          for (int iy = 0; iy < M; ++iy) {
+            const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
+            const TC L = xi[0], R = xi[TX];
+            const TC sv = (iy & 1) ? R - L : R + L;
+            const TC dv = (iy & 1) ? R + L : R - L;
+#pragma unroll
+            for (int gg = 0; gg < NG; ++gg) {
+              const int b = gg - a;
+              if (b < 0 || b >= NA) continue;
+#pragma unroll
+              for (int r = 0; r < M; ++r) acc[gg][r] = fma(co.gy[b][r * 4 + iy], (r & 1) ? dv : sv, acc[gg][r]);
+            }
+          }
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+          for (int r = 0; r < M; ++r) yo[(gg * M * M * M + r * M) * YS] = acc[gg][r];
+      }
     }
     __syncthreads();
     // z-pass.  Plane p is the upper face of cell z0 + p - 1 and the lower face
@@ -199,28 +318,55 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     for (int k = 0; k < ZPT; ++k) {
       if (zxy[k] < 0) continue;
       TC E[2][M], O[2][M];
+      if constexpr (PK) {
+        unsigned long long E2[M], O2[M];  // lanes: f_out = 0, 1
 #pragma unroll
-      for (int fo = 0; fo < 2; ++fo)
+        for (int r = 0; r < M; ++r) E2[r] = O2[r] = 0ull;
 #pragma unroll
-        for (int r = 0; r < M; ++r) E[fo][r] = O[fo][r] = TC(0);
+        for (int fi = 0; fi < 2; ++fi)
 #pragma unroll
-      for (int fi = 0; fi < 2; ++fi)
+          for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
-        for (int gg = 0; gg < NG; ++gg)
-#pragma unroll
-          for (int iz = 0; iz < M; ++iz) {
-            const TC y = sY[zsrc[k] + ((fi * NG + gg) * M + iz) * M * M * YS];
-#pragma unroll
-            for (int fo = 0; fo < 2; ++fo)
+            for (int iz = 0; iz < M; ++iz) {
+              const TC y = sY[zsrc[k] + ((fi * NG + gg) * M + iz) * M * M * YS];
+              const unsigned long long yy = pack2f(y, y);
 #pragma unroll
               for (int r = 0; r < M; ++r) {
-                const TC w = co.kz[fo][fi][gg][r * 4 + iz];
                 if (iz & 1)
-                  O[fo][r] = fma(w, y, O[fo][r]);
+                  O2[r] = fma2f(pc->kz[fi][gg][r][iz], yy, O2[r]);
                 else
-                  E[fo][r] = fma(w, y, E[fo][r]);
+                  E2[r] = fma2f(pc->kz[fi][gg][r][iz], yy, E2[r]);
               }
-          }
+            }
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          unpack2f(E2[r], E[0][r], E[1][r]);
+          unpack2f(O2[r], O[0][r], O[1][r]);
+        }
+      } else {
+#pragma unroll
+        for (int fo = 0; fo < 2; ++fo)
+#pragma unroll
+          for (int r = 0; r < M; ++r) E[fo][r] = O[fo][r] = TC(0);
+#pragma unroll
+        for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+          for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+            for (int iz = 0; iz < M; ++iz) {
+              const TC y = sY[zsrc[k] + ((fi * NG + gg) * M + iz) * M * M * YS];
+#pragma unroll
+              for (int fo = 0; fo < 2; ++fo)
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                  const TC w = co.kz[fo][fi][gg][r * 4 + iz];
+                  if (iz & 1)
+                    O[fo][r] = fma(w, y, O[fo][r]);
+                  else
+                    E[fo][r] = fma(w, y, E[fo][r]);
+                }
+            }
+      }
       if (p > 0) {
         TS *o = out + (size_t)(z0 + p - 1) * pxy + zxy[k] + (size_t)zcomp[k] * plane;
 #pragma unroll
@@ -236,6 +382,11 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   }
 }
 
+// The packed tables travel as a kernel parameter of the FP32 kernels only.
+struct NoPackedCoeffs {};
+template <typename TC>
+using PackedFor = typename std::conditional<std::is_same<TC, float>::value, PackedCoeffs, NoPackedCoeffs>::type;
+
 #define HERMITE_FUSED_KERNEL_BODY                                                                   \
   using Sh = FusedShape<TC, M, TX, TY, G>;                                                          \
   extern __shared__ __align__(16) unsigned char smem_raw[];                                        \
@@ -246,12 +397,15 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   const int y0 = (blockIdx.x / tiles_x) * TY;                                                      \
   const int z0 = g.zlo + blockIdx.y * zchunk;                                                      \
   if (z0 >= g.zhi) return;                                                                         \
-  fused_tile<TS, TC, M, TX, TY, NT, G>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY);
+  constexpr bool PK = std::is_same<TC, float>::value;                                              \
+  const PackedCoeffs *pp = nullptr;                                                                \
+  if constexpr (PK) pp = &pc;                                                                      \
+  fused_tile<TS, TC, M, TX, TY, NT, G, PK>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY, pp);
 
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2>
 __global__ void __launch_bounds__(NT)
     fused_step_kernel(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
-                      const StepCoeffs<TC> co) {
+                      const StepCoeffs<TC> co, const PackedFor<TC> pc) {
   HERMITE_FUSED_KERNEL_BODY
 }
 
@@ -262,7 +416,7 @@ __global__ void __launch_bounds__(NT)
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
     fused_step_kernel_mb(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
-                         const StepCoeffs<TC> co) {
+                         const StepCoeffs<TC> co, const PackedFor<TC> pc) {
   HERMITE_FUSED_KERNEL_BODY
 }
 
@@ -287,7 +441,9 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
   if (zchunk <= 0) zchunk = 16;
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
   dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
-  kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co);
+  PackedFor<TC> pc{};
+  if constexpr (std::is_same<TC, float>::value) pc = pack_coeffs(co);
+  kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co, pc);
   return cudaGetLastError();
 }
 
