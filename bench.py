@@ -414,6 +414,16 @@ def run_advection(torch, rank, world, max_over_ranks, hbm_peak, side=150, nsteps
                             "value": world * dof / (half_ms * 1e-3), "unit": "DOF-updates/s",
                             "hbm_gbs_algorithmic": bytes_alg / (half_ms * 1e-3) / 1e9,
                             "hbm_frac": bytes_alg / (half_ms * 1e-3) / 1e9 / hbm_peak}
+            if variant == "fused":
+                # the same 2 nsteps half steps in FP64 from the same state: error of the FP32 run
+                p64 = AdvectionPlan(m, (side,) * 3, h, (1.0, 1.0, 1.0), 0.9 * h[0], prec="fp64", state="fp64")
+                a64, b64 = x0.double(), torch.empty(x0.shape, dtype=torch.float64, device="cuda")
+                for k in range(2 * nsteps):
+                    p64.step(a64, b64, k % 2)
+                    a64, b64 = b64, a64
+                (max_abs, max_rel, rms, l2_rel), _ = plan.error(a, a64, mask=0b101)
+                row["fp32_vs_fp64_end_state"] = {"max_rel_all_components": max_rel, "l2_rel": l2_rel}
+                del p64, a64, b64
             del plan
         key = {"fused": "monolithic", "split": "two_kernels"}
         row["speedup_vs_paper"] = {v: TABLE1_SECONDS[m][key[v]] / row[v]["seconds_to_solution"] for v in key}
