@@ -17,8 +17,10 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "advect.h"
+#include "packed_f32.cuh"
 
 namespace hermite {
 
@@ -206,10 +208,30 @@ struct FusedAdvShape {
   static constexpr size_t BYTES = ((size_t)SX + SY) * sizeof(TC);
 };
 
+// FP32 kernels: the 1-D factors as duplicated pairs (g, g), so that one
+// fma.rn.f32x2 applies a coefficient to two independent inputs (two x-pass
+// items, or two r1 rows of the y- and z-passes).
+struct AdvPacked {
+  unsigned long long g[3][kAdvMaxP][kAdvMaxP];
+};
+struct NoAdvPacked {};
+template <typename TC>
+using AdvPackedFor = typename std::conditional<std::is_same<TC, float>::value, AdvPacked, NoAdvPacked>::type;
+
+inline AdvPacked pack_adv(const KronCoeffs<float> &c) {
+  AdvPacked p{};
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < kAdvMaxP; ++r)
+      for (int q = 0; q < kAdvMaxP; ++q) p.g[k][r][q] = pack_pair_host(c.g[k][r][q], c.g[k][r][q]);
+  return p;
+}
+
 template <typename TS, typename TC, int M, int TX, int TY, int XC>
 __global__ void __launch_bounds__(TY * M * TX)
-    adv_fused_kernel(const TS *__restrict__ in, TS *__restrict__ out, Geom g, KronCoeffs<TC> co, int zchunk) {
+    adv_fused_kernel(const TS *__restrict__ in, TS *__restrict__ out, Geom g, KronCoeffs<TC> co, int zchunk,
+                     const AdvPackedFor<TC> pk) {
   using S = FusedAdvShape<TS, TC, M, TX, TY>;
+  constexpr bool PKA = std::is_same<TC, float>::value;  // packed f32x2 passes
   constexpr int P = S::P, NT = S::NT;
   constexpr int XI = (TY + 1) * M * M * TX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -234,13 +256,14 @@ __global__ void __launch_bounds__(TY * M * TX)
   const bool xin = x0 + xc < nx;
   const int xl = wrap1(x0 + xc + s, nx), xr = wrap1(x0 + xc + s + 1, nx);
   TC acc[M][M];  // pending cell: [r1][r3]
+  unsigned long long accp[M / 2 > 0 ? M / 2 : 1][M];  // FP32: rows (2 r1p, 2 r1p + 1) packed
   for (int L = 0; L < nl; ++L) {
     const int zn = wrap1(zb + s + L, nz);
     // x-pass: items (node row, i3, i2, x), IT per thread, taken in chunks of
     // XC items whose loads are all issued before the first product
 #pragma unroll
     for (int i0 = 0; i0 < IT; i0 += XC) {
-      TS v[XC][P];
+      TS v[XC][P] = {};
 #pragma unroll
       for (int j = 0; j < XC; ++j) {
         const int e = threadIdx.x + (i0 + j) * NT;
@@ -255,27 +278,78 @@ __global__ void __launch_bounds__(TY * M * TX)
           v[j][M + i1] = __ldg(base + (size_t)i1 * N + xr);
         }
       }
+      if constexpr (PKA && XC == 2) {  // the two items on the packed lanes
+        bool ok[2];
+        int doff[2];
 #pragma unroll
-      for (int j = 0; j < XC; ++j) {
-        const int e = threadIdx.x + (i0 + j) * NT;
-        const int t = e / TX;
-        const int i2 = t % M, i3 = (t / M) % M, yn = t / (M * M);
-        if (i0 + j >= IT || e >= XI || !xin || y0 + yn > ny) continue;
-        TC *dst = sX + ((yn * M + i3) * M + i2) * M * TX + xc;
+        for (int j = 0; j < 2; ++j) {
+          const int e = threadIdx.x + (i0 + j) * NT;
+          const int t = e / TX;
+          const int i2 = t % M, i3 = (t / M) % M, yn = t / (M * M);
+          ok[j] = i0 + j < IT && e < XI && xin && y0 + yn <= ny;
+          doff[j] = ((yn * M + i3) * M + i2) * M * TX + xc;
+        }
+        unsigned long long vv[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) vv[c] = pack2f((TC)v[0][c], (TC)v[1][c]);
 #pragma unroll
         for (int r = 0; r < M; ++r) {
-          TC a = co.g[0][r][0] * (TC)v[j][0];
+          unsigned long long a = mul2f(pk.g[0][r][0], vv[0]);
 #pragma unroll
-          for (int c = 1; c < P; ++c) a = fma(co.g[0][r][c], (TC)v[j][c], a);
-          dst[r * TX] = a;
+          for (int c = 1; c < P; ++c) a = fma2f(pk.g[0][r][c], vv[c], a);
+          float lo, hi;
+          unpack2f(a, lo, hi);
+          if (ok[0]) sX[doff[0] + r * TX] = lo;
+          if (ok[1]) sX[doff[1] + r * TX] = hi;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < XC; ++j) {
+          const int e = threadIdx.x + (i0 + j) * NT;
+          const int t = e / TX;
+          const int i2 = t % M, i3 = (t / M) % M, yn = t / (M * M);
+          if (i0 + j >= IT || e >= XI || !xin || y0 + yn > ny) continue;
+          TC *dst = sX + ((yn * M + i3) * M + i2) * M * TX + xc;
+#pragma unroll
+          for (int r = 0; r < M; ++r) {
+            TC a = co.g[0][r][0] * (TC)v[j][0];
+#pragma unroll
+            for (int c = 1; c < P; ++c) a = fma(co.g[0][r][c], (TC)v[j][c], a);
+            dst[r * TX] = a;
+          }
         }
       }
     }
     __syncthreads();
     // y-pass: column (yc, i3 = k, x), loop over r1
     if (live) {
+      constexpr int RP1 = PKA ? M / 2 : 0;  // r1 pairs on the packed lanes
+      if constexpr (PKA) {
 #pragma unroll
-      for (int r1 = 0; r1 < M; ++r1) {
+        for (int rp = 0; rp < RP1; ++rp) {
+          unsigned long long vv[P];
+#pragma unroll
+          for (int side = 0; side < 2; ++side)
+#pragma unroll
+            for (int i2 = 0; i2 < M; ++i2) {
+              const TC *src = sX + ((((yc + side) * M + k) * M + i2) * M + 2 * rp) * TX + xc;
+              vv[side * M + i2] = pack2f(src[0], src[TX]);
+            }
+          TC *dst = sY + ((yc * M + k) * M * M + 2 * rp) * TX + xc;
+#pragma unroll
+          for (int r2 = 0; r2 < M; ++r2) {
+            unsigned long long a = mul2f(pk.g[1][r2][0], vv[0]);
+#pragma unroll
+            for (int c = 1; c < P; ++c) a = fma2f(pk.g[1][r2][c], vv[c], a);
+            float lo, hi;
+            unpack2f(a, lo, hi);
+            dst[r2 * M * TX] = lo;
+            dst[r2 * M * TX + TX] = hi;
+          }
+        }
+      }
+#pragma unroll
+      for (int r1 = 2 * RP1; r1 < M; ++r1) {
         TC v[P];
 #pragma unroll
         for (int side = 0; side < 2; ++side)
@@ -296,8 +370,40 @@ __global__ void __launch_bounds__(TY * M * TX)
     // face of cell zb + L - 1 and the lower face of cell zb + L
     if (live) {
       const size_t zoff = (size_t)(zb + L - 1) * ny * nx;
+      constexpr int RP1 = PKA ? M / 2 : 0;
+      if constexpr (PKA) {
 #pragma unroll
-      for (int r1 = 0; r1 < M; ++r1) {
+        for (int rp = 0; rp < RP1; ++rp) {
+          unsigned long long vv[M];
+#pragma unroll
+          for (int i3 = 0; i3 < M; ++i3) {
+            const TC *src = sY + (((yc * M + i3) * M + k) * M + 2 * rp) * TX + xc;
+            vv[i3] = pack2f(src[0], src[TX]);
+          }
+          if (L > 0) {
+#pragma unroll
+            for (int r3 = 0; r3 < M; ++r3) {
+              unsigned long long a = accp[rp][r3];
+#pragma unroll
+              for (int i3 = 0; i3 < M; ++i3) a = fma2f(pk.g[2][r3][M + i3], vv[i3], a);
+              float lo, hi;
+              unpack2f(a, lo, hi);
+              const size_t o = out_col + (size_t)(r3 * M * M + 2 * rp) * N + zoff;
+              out[o] = (TS)lo;
+              out[o + N] = (TS)hi;
+            }
+          }
+#pragma unroll
+          for (int r3 = 0; r3 < M; ++r3) {
+            unsigned long long a = mul2f(pk.g[2][r3][0], vv[0]);
+#pragma unroll
+            for (int i3 = 1; i3 < M; ++i3) a = fma2f(pk.g[2][r3][i3], vv[i3], a);
+            accp[rp][r3] = a;
+          }
+        }
+      }
+#pragma unroll
+      for (int r1 = 2 * RP1; r1 < M; ++r1) {
         TC v[M];
 #pragma unroll
         for (int i3 = 0; i3 < M; ++i3) v[i3] = sY[(((yc * M + i3) * M + k) * M + r1) * TX + xc];
@@ -343,7 +449,9 @@ cudaError_t launch_fused_adv(const TS *in, TS *out, const Geom &g, const KronCoe
   if ((nzc + zc - 1) / zc > 65535) zc = (nzc + 65534) / 65535;  // gridDim.z limit
   if (nzc <= 0 || g.nx <= 0 || g.ny <= 0) return cudaSuccess;
   dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (nzc + zc - 1) / zc);
-  kern<<<grid, S::NT, smem, st>>>(in, out, g, co, zc);
+  AdvPackedFor<TC> pk{};
+  if constexpr (std::is_same<TC, float>::value) pk = pack_adv(co);
+  kern<<<grid, S::NT, smem, st>>>(in, out, g, co, zc, pk);
   return cudaGetLastError();
 }
 

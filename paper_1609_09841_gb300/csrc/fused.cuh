@@ -31,6 +31,7 @@
 #include <type_traits>
 
 #include "hermite_impl.h"
+#include "packed_f32.cuh"
 
 namespace hermite {
 
@@ -60,13 +61,6 @@ struct PackedCoeffs {
   unsigned long long kz[2][kMaxG][4][4];  // [f_in][g][r][iz]: (kz[0][f_in][g][r*4+iz], kz[1][f_in][g][r*4+iz])
 };
 
-inline unsigned long long pack_pair_host(float lo, float hi) {
-  unsigned a, b;
-  std::memcpy(&a, &lo, 4);
-  std::memcpy(&b, &hi, 4);
-  return ((unsigned long long)b << 32) | a;
-}
-
 inline PackedCoeffs pack_coeffs(const StepCoeffs<float> &c) {
   PackedCoeffs p{};
   for (int a = 0; a < kMaxA; ++a)
@@ -81,20 +75,6 @@ inline PackedCoeffs pack_coeffs(const StepCoeffs<float> &c) {
         for (int iz = 0; iz < 4; ++iz)
           p.kz[fi][g][r][iz] = pack_pair_host(c.kz[0][fi][g][r * 4 + iz], c.kz[1][fi][g][r * 4 + iz]);
   return p;
-}
-
-__device__ __forceinline__ unsigned long long pack2f(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void unpack2f(unsigned long long v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long fma2f(unsigned long long a, unsigned long long b, unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
 }
 
 __device__ __forceinline__ int wrap_index(int v, int n) {
