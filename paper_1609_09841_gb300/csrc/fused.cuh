@@ -42,7 +42,13 @@ struct FusedShape {
   static constexpr int NYN = TY + 1;
   static constexpr int NA = (M - 1 < G ? M - 1 : G) + 1;   // grades a <= min(m, G) of the 1-D factors
   static constexpr int NG = (2 * (NA - 1) < G ? 2 * (NA - 1) : G) + 1;  // grades of the y-pass results
-  static constexpr int SX = 2 * M * M * NA * M * NYN * TX;  // x-pass results [f][iz][iy][a][ix'][ey][ex]
+  // x-pass results [f][iz][iy][a][ix'][ey][ex], one block of XB words per (f, iz, iy).  XB is
+  // padded to NYN * TX modulo 32 words, so that a warp whose items run from the last node rows
+  // of one block into the next one stores to consecutive banks.
+  static constexpr int XB0 = NA * M * NYN * TX;
+  static constexpr int XPAD = (((NYN * TX - XB0) % 32) + 32) % 32;
+  static constexpr int XB = XB0 + XPAD;
+  static constexpr int SX = 2 * M * M * XB;
   static constexpr int SY = 2 * NG * M * M * M * TX * TY;   // y-pass results [f][g][iz][iy'][ix'][fy][fx]
   static constexpr size_t SMEM = (size_t)(SX + SY) * sizeof(TC);  // one plane of y-pass results
   static constexpr int XITEMS = 2 * M * M * NYN * TX;       // (f, iz, iy, edge)
@@ -121,7 +127,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     xsrc[k] = in + (size_t)(((f * M + iz) * M + iy) * M) * plane;
     xl[k] = gy * nx + wrap_index(x0 + s + ex, nx);
     xr[k] = gy * nx + wrap_index(x0 + s + ex + 1, nx);
-    xdst[k] = e < Sh::XITEMS ? (((f * M + iz) * M + iy) * NA * M) * XS + ey * TX + ex : -1;
+    xdst[k] = e < Sh::XITEMS ? ((f * M + iz) * M + iy) * Sh::XB + ey * TX + ex : -1;
   }
   // y-items: base of the two edges in sX and of the face in sY.
   int ysrc[YPT], ydst[YPT];
@@ -134,7 +140,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     const int ixp = t % M; t /= M;
     const int iz = t % M;
     const int f = t / M;
-    ysrc[k] = ((f * M + iz) * M * NA * M + ixp) * XS + fy * TX + fx;
+    ysrc[k] = (f * M + iz) * M * Sh::XB + ixp * XS + fy * TX + fx;
     ydst[k] = e < Sh::YITEMS ? ((f * NG * M + iz) * M * M + ixp) * YS + fy * TX + fx : -1;
   }
   // z-items: base in sY and the output node's in-plane offset (-1 if outside).
@@ -233,7 +239,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         for (int a = 0; a < NA; ++a)
 #pragma unroll
           for (int iy = 0; iy < M; ++iy) {
-            const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
+            const TC *xi = sX + ysrc[k] + iy * Sh::XB + a * M * XS;
             const TC L = xi[0], R = xi[TX];
             const TC sv = (iy & 1) ? R - L : R + L;
             const TC dv = (iy & 1) ? R + L : R - L;
@@ -268,7 +274,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         for (int a = 0; a < NA; ++a)
 #pragma unroll
           for (int iy = 0; iy < M; ++iy) {
-            const TC *xi = sX + ysrc[k] + (iy * NA + a) * M * XS;
+            const TC *xi = sX + ysrc[k] + iy * Sh::XB + a * M * XS;
             const TC L = xi[0], R = xi[TX];
             const TC sv = (iy & 1) ? R - L : R + L;
             const TC dv = (iy & 1) ? R + L : R - L;
