@@ -135,9 +135,18 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   for (int k = 0; k < YPT; ++k) {
     const int e = threadIdx.x + k * NT;
     int t = e < Sh::YITEMS ? e : 0;
-    const int fx = t % TX; t /= TX;
-    const int fy = t % TY; t /= TY;
-    const int ixp = t % M; t /= M;
+    // item order (fx, fy, ix') when a warp holds whole (f, iz, ix') rows of faces; for smaller
+    // tiles (fx, ix', fy), so that the warp's sX reads (ix' stride XS) fall on distinct banks
+    int fx, fy, ixp;
+    if constexpr (TX * TY < 32) {
+      fx = t % TX; t /= TX;
+      ixp = t % M; t /= M;
+      fy = t % TY; t /= TY;
+    } else {
+      fx = t % TX; t /= TX;
+      fy = t % TY; t /= TY;
+      ixp = t % M; t /= M;
+    }
     const int iz = t % M;
     const int f = t / M;
     ysrc[k] = (f * M + iz) * M * Sh::XB + ixp * XS + fy * TX + fx;
