@@ -37,8 +37,8 @@ FLOP_PER_NODE = {m: 2 * 30 * (m + 1) ** 4 + 28 * (m + 1) ** 3 for m in (1, 2, 3)
 # FP32 SIMT peak of a GB300 at its maximum SM clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 kernel (ncu capture of the
-# 8x2x256 schedule the autotuner picks, at 128^3: 2.233 GB, scaled by the node count x 8).
-TRAFFIC_BYTES = {(3, 256): 17.86e9}
+# 8x2x256 schedule the autotuner picks, at 128^3: 2.244 GB, scaled by the node count x 8).
+TRAFFIC_BYTES = {(3, 256): 17.95e9}
 FP64_PEAK_TFLOPS = 1.25
 
 

@@ -42,11 +42,12 @@ struct FusedShape {
   static constexpr int NYN = TY + 1;
   static constexpr int NA = (M - 1 < G ? M - 1 : G) + 1;   // grades a <= min(m, G) of the 1-D factors
   static constexpr int NG = (2 * (NA - 1) < G ? 2 * (NA - 1) : G) + 1;  // grades of the y-pass results
-  // x-pass results [f][iz][iy][a][ix'][ey][ex], one block of XB words per (f, iz, iy).  XB is
-  // padded to NYN * TX modulo 32 words, so that a warp whose items run from the last node rows
-  // of one block into the next one stores to consecutive banks.
+  // x-pass results [f][iz][iy][a][ix'][ey][ex], one block of XB words per (f, iz, iy).  For the
+  // RK4 kernels XB is padded to NYN * TX modulo 32 words, so that a warp whose items run from
+  // the last node rows of one block into the next one stores to consecutive banks (the longer
+  // series' kernels, at lower occupancy, measured slower with the padding).
   static constexpr int XB0 = NA * M * NYN * TX;
-  static constexpr int XPAD = (((NYN * TX - XB0) % 32) + 32) % 32;
+  static constexpr int XPAD = G == 2 ? (((NYN * TX - XB0) % 32) + 32) % 32 : 0;  // (longer series: no gain)
   static constexpr int XB = XB0 + XPAD;
   static constexpr int SX = 2 * M * M * XB;
   static constexpr int SY = 2 * NG * M * M * M * TX * TY;   // y-pass results [f][g][iz][iy'][ix'][fy][fx]
