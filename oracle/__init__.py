@@ -23,7 +23,8 @@ Modules: ``hermite`` (the half step, its adjoint, norms, energy),
 ``exact`` (closed-form solutions sampled as scaled derivatives) and
 ``symbol`` (Fourier symbol and stability limit of the half step).
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
-``hermite.energy``, which is parity unpinned (the paper does not define the
-energy it would conserve; the check in the tests is a proposed invariant).
+Parity status: every function is pinned by ``tests/test_oracle_*.py``.
+``hermite.energy`` (the paper defines no energy; this one is the wave
+equation's quadratic invariant on the interpolants) is pinned by quadrature
+of an independently built interpolant and by a closed form.
 """

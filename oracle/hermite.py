@@ -428,8 +428,10 @@ def error_norms(a, b, component_mask=0b111):
 def energy(S, m, h, c, parity_of_grid=0):
     """E = sum over cells of the integral over the cell of B_v^2 + c^2 |grad B_u|^2,
     B the interpolant of the current data (Eq. 3) on each cell of the current
-    grid.  Parity unpinned: the paper defines no energy; this is the natural
-    quadratic invariant of the wave equation evaluated on the interpolants."""
+    grid.  The paper defines no energy; this is the natural quadratic
+    invariant of the wave equation evaluated on the interpolants.  Pinned by
+    a Gauss-Legendre quadrature of SciPy's Hermite interpolant and by the
+    closed-form energy of a standing mode (tests/test_oracle_energy.py)."""
     M, P = m + 1, 2 * m + 2
     H = hermite_matrix(m)
     U = gather_cells(S, m, parity_of_grid)
