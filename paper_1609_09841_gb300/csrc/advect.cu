@@ -529,7 +529,7 @@ cudaError_t launch_evolve_adv(const TC *ws, TS *out, const Geom &g, int z0, int 
   return cudaGetLastError();
 }
 
-// Tile tables (TX x TY cells per CTA), two shapes per order and precision
+// Tile tables (TX x TY cells per CTA), three shapes per order and precision
 // for the fused kernel (the plan's schedule picks one) and one for the
 // interpolation kernel; every shape stays within 227 KB of shared memory
 // (checked at compile time).
@@ -552,12 +552,33 @@ cudaError_t fused_dispatch_xc(int m, bool b, const TS *i, TS *o, const Geom &g, 
   return cudaErrorInvalidValue;
 }
 
-// tile = 2 * (loads of two x-pass items in flight) + (taller CTA)
+// Shapes whose x-pass items, (TY + 1) M^2 TX of them, split evenly over the
+// TY M TX threads: TY divides M, so no thread is left with a partial last
+// chunk while the rest of the CTA waits at the barrier.  TY = 2 and 3 for
+// m = 1 and 2; for m = 3 the even shapes not in the table above (FP32 one
+// row, FP64 four).
+template <typename TS, typename TC, int XC>
+cudaError_t fused_dispatch_even(int m, const TS *i, TS *o, const Geom &g, const KronCoeffs<TC> &co, int zchunk,
+                                cudaStream_t st) {
+  constexpr bool d = sizeof(TC) == 8;
+  switch (m) {
+    case 1: return launch_fused_adv<TS, TC, 2, 32, 2, XC>(i, o, g, co, zchunk, st);
+    case 2: return launch_fused_adv<TS, TC, 3, 32, 3, XC>(i, o, g, co, zchunk, st);
+    case 3: return launch_fused_adv<TS, TC, 4, 32, d ? 4 : 1, XC>(i, o, g, co, zchunk, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// tile 0-3 = 2 * (loads of two x-pass items in flight) + (taller CTA);
+// tiles 4, 5 = the even shapes with one or two items in flight
 template <typename TS, typename TC>
 cudaError_t fused_dispatch(int m, int tile, const void *in, void *out, const Geom &g, const KronCoeffs<TC> &co,
                            int zchunk, cudaStream_t st) {
   const TS *i = static_cast<const TS *>(in);
   TS *o = static_cast<TS *>(out);
+  if (tile >= 4)
+    return tile == 5 ? fused_dispatch_even<TS, TC, 2>(m, i, o, g, co, zchunk, st)
+                     : fused_dispatch_even<TS, TC, 1>(m, i, o, g, co, zchunk, st);
   const bool b = (tile & 1) != 0;
   return tile >= 2 ? fused_dispatch_xc<TS, TC, 2>(m, b, i, o, g, co, zchunk, st)
                    : fused_dispatch_xc<TS, TC, 1>(m, b, i, o, g, co, zchunk, st);

@@ -51,7 +51,7 @@ void build_adv_coeffs(int m, const double h[3], const double a[3], double tau, K
 // Fused half step for output cells z in [g.zlo, g.zhi).  state / compute:
 // kF32 or kF64 (compute kF64 needs state kF64); tile < kAdvFusedTiles picks
 // one of the compiled CTA shapes.
-constexpr int kAdvFusedTiles = 4;
+constexpr int kAdvFusedTiles = 6;
 cudaError_t launch_adv_fused(int m, int tile, int state, int compute, const void *in, void *out, const Geom &g,
                              const KronCoeffs<double> &cd, const KronCoeffs<float> &cf, int zchunk, cudaStream_t st);
 // Split pair on the z-slab of cells [z0, z0 + nzl): interpolation into the

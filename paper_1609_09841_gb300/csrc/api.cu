@@ -489,8 +489,10 @@ int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double
   p->adv_ev.tau = tau;
   for (int k = 0; k < 3; ++k) p->adv_ev.ah[k] = a[k] / h[k];
   p->adv_ev.q = q;
-  // fastest fused schedules measured at 150^3 on GB300 (hermite_set_schedule overrides)
-  p->tile = prec == HERMITE_FP64 ? 1 : (m == 3 ? 3 : (m == 1 ? 2 : 0));
+  // fastest fused schedules measured at 150^3 on GB300, [FP64?][m - 1]
+  // (hermite_set_schedule overrides)
+  static const int kAdvDefaultTile[2][3] = {{5, 5, 3}, {1, 5, 4}};
+  p->tile = kAdvDefaultTile[prec == HERMITE_FP64 ? 1 : 0][m - 1];
   p->zchunk = 16;
   p->ws_limit = (size_t)1 << 30;
   *out = p;

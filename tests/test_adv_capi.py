@@ -40,9 +40,9 @@ def test_adv_plan_accepts_and_refuses_wave_only_calls(capi):
     rc, p = _adv(capi, m=2, grid=(6, 5, 4))
     assert rc == 0
     assert capi.lib.hermite_state_elems(p) == 27 * 6 * 5 * 4
-    assert capi.lib.hermite_schedule_count(p) == 4     # fused: two CTA heights x two load depths
-    assert capi.lib.hermite_set_schedule(p, 3, 4) == 0
-    assert capi.lib.hermite_set_schedule(p, 4, 4) == -1
+    assert capi.lib.hermite_schedule_count(p) == 6     # fused: three CTA heights x two load depths
+    assert capi.lib.hermite_set_schedule(p, 5, 4) == 0
+    assert capi.lib.hermite_set_schedule(p, 6, 4) == -1
     assert capi.lib.hermite_set_taylor_order(p, 6) == -4
     assert capi.lib.hermite_adjoint_step(p, None, None, 0, None) == -4
     assert capi.lib.hermite_step_dc(p, None, None, 0, None) == -4
