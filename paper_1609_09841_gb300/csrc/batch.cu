@@ -7,16 +7,22 @@
 // another, so there is nothing to time out.
 #include <cuda_runtime.h>
 
+#include <cstring>
+#include <type_traits>
+
 #include "batch.h"
 #include "fused.cuh"
 
 namespace hermite {
 
 // Tile shapes of the batched kernel per order (NT = 256 threads for all).
+// At m = 3 the 8 x 2 tile gives every thread exactly 3 x-pass, 2 y-pass and
+// 1 z-pass items (a 4 x 4 tile left a partial third x-pass chunk); m = 1 and
+// 2 cannot split evenly over 256 threads with tiles that divide the grids.
 template <int M> struct BatchTile;
 template <> struct BatchTile<2> { static constexpr int TX = 8, TY = 8; };
 template <> struct BatchTile<3> { static constexpr int TX = 8, TY = 4; };
-template <> struct BatchTile<4> { static constexpr int TX = 4, TY = 4; };
+template <> struct BatchTile<4> { static constexpr int TX = 8, TY = 2; };
 constexpr int kBatchThreads = 256;
 // Resident CTAs per SM the compiler must fit the batched kernel's registers to.
 #ifndef HERMITE_BATCH_MIN_BLOCKS
@@ -31,18 +37,53 @@ void batch_tile_shape(int m, int *tx, int *ty) {
   }
 }
 
+// Per-simulation table record: StepCoeffs<TC>, and for FP32 arithmetic the
+// same tables as packed pairs (PackedCoeffs) right after it, so that the tile
+// body runs its fma.rn.f32x2 path with the pairs read from shared memory.
+template <typename TC>
+constexpr bool kBatchPacked = std::is_same<TC, float>::value;
+
+template <typename TC>
+constexpr size_t batch_record_bytes() {
+  return sizeof(StepCoeffs<TC>) + (kBatchPacked<TC> ? sizeof(PackedCoeffs) : 0);
+}
+
+static_assert(sizeof(StepCoeffs<float>) % 8 == 0 && sizeof(StepCoeffs<double>) % 8 == 0 &&
+                  sizeof(PackedCoeffs) % 8 == 0,
+              "table records are copied in 8-byte words and the packed pairs read as 8-byte values");
+
+size_t batch_coeff_record_bytes(int compute) {
+  return compute == kF64 ? batch_record_bytes<double>() : batch_record_bytes<float>();
+}
+
+void batch_write_record(int compute, const StepCoeffs<double> &cd, unsigned char *dst) {
+  if (compute == kF64) {
+    std::memcpy(dst, &cd, sizeof(cd));
+    return;
+  }
+  const StepCoeffs<float> cf = cast_coeffs<float>(cd);
+  const PackedCoeffs pc = pack_coeffs(cf);
+  std::memcpy(dst, &cf, sizeof(cf));
+  std::memcpy(dst + sizeof(cf), &pc, sizeof(pc));
+}
+
+template <typename TC>
+constexpr size_t batch_tables_bytes() {  // the record in shared memory, 16-byte aligned
+  return (batch_record_bytes<TC>() + 15) / 16 * 16;
+}
+
 template <typename TC>
 constexpr size_t batch_smem_bytes() {
   constexpr size_t a = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>::SMEM;
   constexpr size_t b = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>::SMEM;
   constexpr size_t c = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>::SMEM;
   constexpr size_t mx = a > b ? (a > c ? a : c) : (b > c ? b : c);
-  return mx + sizeof(StepCoeffs<TC>);
+  return mx + batch_tables_bytes<TC>();
 }
 
 template <typename TS, typename TC, int M>
 __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
-                                           TC *sX, TC *sY, int s) {
+                                           const PackedCoeffs *pc, TC *sX, TC *sY, int s) {
   constexpr int TX = BatchTile<M>::TX, TY = BatchTile<M>::TY;
   Geom g;
   g.nx = sm.n[0];
@@ -54,16 +95,19 @@ __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
   const int z0 = it.z0, z1 = min(it.z0 + sm.zchunk, g.nz);
-  fused_tile<TS, TC, M, TX, TY, kBatchThreads>((const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sY);
+  fused_tile<TS, TC, M, TX, TY, kBatchThreads, 2, kBatchPacked<TC>>((const TS *)sm.in, (TS *)sm.out, g, x0, y0,
+                                                                    z0, z1, co, sX, sY, pc);
 }
 
 template <typename TS, typename TC>
 __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
-    batch_step_kernel(const BatchSim *__restrict__ sims, const StepCoeffs<TC> *__restrict__ coeffs,
+    batch_step_kernel(const BatchSim *__restrict__ sims, const unsigned char *__restrict__ coeffs,
                       const BatchItem *__restrict__ items, int nitems, int *__restrict__ counter, int s) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StepCoeffs<TC> *sco = reinterpret_cast<StepCoeffs<TC> *>(smem_raw);
-  TC *sX = reinterpret_cast<TC *>(smem_raw + ((sizeof(StepCoeffs<TC>) + 15) / 16) * 16);
+  const PackedCoeffs *spc =
+      kBatchPacked<TC> ? reinterpret_cast<const PackedCoeffs *>(smem_raw + sizeof(StepCoeffs<TC>)) : nullptr;
+  TC *sX = reinterpret_cast<TC *>(smem_raw + batch_tables_bytes<TC>());
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -72,26 +116,27 @@ __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
     if (i >= nitems) break;
     const BatchItem it = items[i];
     const BatchSim sm = sims[it.sim];
-    {
-      const TC *src = reinterpret_cast<const TC *>(coeffs + it.sim);
-      TC *dst = reinterpret_cast<TC *>(sco);
-      for (int k = threadIdx.x; k < (int)(sizeof(StepCoeffs<TC>) / sizeof(TC)); k += kBatchThreads) dst[k] = src[k];
+    {  // the simulation's table record, in 8-byte words (both parts are multiples of 8 bytes)
+      const unsigned long long *src =
+          reinterpret_cast<const unsigned long long *>(coeffs + (size_t)it.sim * batch_record_bytes<TC>());
+      unsigned long long *dst = reinterpret_cast<unsigned long long *>(smem_raw);
+      for (int k = threadIdx.x; k < (int)(batch_record_bytes<TC>() / 8); k += kBatchThreads) dst[k] = src[k];
     }
     __syncthreads();
     switch (sm.m) {
       case 1: {
         using Sh = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>;
-        batch_tile<TS, TC, 2>(sm, it, *sco, sX, sX + Sh::SX, s);
+        batch_tile<TS, TC, 2>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
         break;
       }
       case 2: {
         using Sh = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>;
-        batch_tile<TS, TC, 3>(sm, it, *sco, sX, sX + Sh::SX, s);
+        batch_tile<TS, TC, 3>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
         break;
       }
       default: {
         using Sh = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>;
-        batch_tile<TS, TC, 4>(sm, it, *sco, sX, sX + Sh::SX, s);
+        batch_tile<TS, TC, 4>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
         break;
       }
     }
@@ -117,7 +162,7 @@ static cudaError_t launch_batch_t(const BatchSim *sims, const void *coeffs, cons
   }
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kBatchThreads, smem, st>>>(sims, (const StepCoeffs<TC> *)coeffs, items, nitems, counter, s);
+  kern<<<grid, kBatchThreads, smem, st>>>(sims, (const unsigned char *)coeffs, items, nitems, counter, s);
   return cudaGetLastError();
 }
 

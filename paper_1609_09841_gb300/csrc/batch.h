@@ -24,6 +24,10 @@ struct BatchItem {     // one unit of work: a TX x TY x zchunk block of one simu
 };
 
 void batch_tile_shape(int m, int *tx, int *ty);
+// One simulation's table record as the kernel reads it (compute kF32:
+// StepCoeffs<float> then its PackedCoeffs; kF64: StepCoeffs<double>).
+size_t batch_coeff_record_bytes(int compute);
+void batch_write_record(int compute, const StepCoeffs<double> &cd, unsigned char *dst);
 int batch_blocks_per_sm(int compute, int state);
 cudaError_t launch_batch(int compute, int state, const BatchSim *sims, const void *coeffs, const BatchItem *items,
                          int nitems, int *counter, int s, int grid, cudaStream_t st);

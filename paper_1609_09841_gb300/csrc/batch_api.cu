@@ -33,7 +33,7 @@ struct BatchPlan {
   std::vector<int> n;           // 3 per simulation
   std::vector<size_t> elems;
   int zchunk[4] = {0, 16, 16, 16};  // per order
-  void *coeffs = nullptr;       // device StepCoeffs<TC>[nsims]
+  void *coeffs = nullptr;       // device table records, one per simulation (batch_write_record)
   BatchItem *items = nullptr;   // device work list
   int nitems = 0;
   int *counter = nullptr;
@@ -184,19 +184,14 @@ int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *
   b->m.assign(m, m + nsims);
   b->n.assign(grid, grid + 3 * nsims);
   b->zc.assign(nsims, 16);
-  const size_t csize = prec == HERMITE_FP64 ? sizeof(StepCoeffs<double>) : sizeof(StepCoeffs<float>);
+  const size_t csize = batch_coeff_record_bytes(b->compute);
   std::vector<unsigned char> host(csize * nsims);
   for (int i = 0; i < nsims; ++i) {
     b->elems.push_back((size_t)2 * (m[i] + 1) * (m[i] + 1) * (m[i] + 1) * grid[3 * i] * grid[3 * i + 1] *
                        grid[3 * i + 2]);
     StepCoeffs<double> cd;
     build_step_coeffs(m[i], h + 3 * i, c[i], 0.5 * dt[i], kForward, 4, &cd);
-    if (prec == HERMITE_FP64) {
-      std::memcpy(host.data() + csize * i, &cd, csize);
-    } else {
-      const StepCoeffs<float> cf = cast_coeffs<float>(cd);
-      std::memcpy(host.data() + csize * i, &cf, csize);
-    }
+    batch_write_record(b->compute, cd, host.data() + csize * i);
   }
   cudaError_t e = cudaMalloc(&b->coeffs, host.size());
   if (e == cudaSuccess) e = cudaMemcpy(b->coeffs, host.data(), host.size(), cudaMemcpyHostToDevice);
