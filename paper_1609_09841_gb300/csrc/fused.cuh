@@ -35,6 +35,10 @@
 
 namespace hermite {
 
+// L1 prefetch hint (PTX prefetch.global.L1): fetches the line holding p into
+// L1 without a register result.  Callers pass addresses they later load.
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // G: largest total grade the kernel carries (2 for the 4-term series of RK4;
 // 2m for longer series, whose higher grades the z-pass tables fold in).
 template <typename TC, int M, int TX, int TY, int G = 2>
@@ -96,7 +100,10 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // put a __syncthreads() between the calls).
 // PK: FP32 passes with fma.rn.f32x2 on the packed tables `pc` (kernel
 // parameters); bitwise the same results as the scalar FMAs.
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false>
+// PF: prefetch the next plane's x-pass lines into L1 during the y- and
+// z-passes (measured faster for the batched kernel's small grids, slower for
+// the single-grid kernels).
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, bool PF = false>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
                                            TC *__restrict__ sX, TC *__restrict__ sY,
@@ -231,6 +238,19 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
       }
     }
     __syncthreads();
+    if constexpr (PF) {
+      // the next plane's x-pass lines into L1 while this plane's y- and
+      // z-passes run (the left nodes cover all but one x-node per row)
+      if (p < z1 - z0) {
+        const size_t znext = (size_t)wrap_index(z0 + s + p + 1, nz) * pxy;
+#pragma unroll
+        for (int k = 0; k < XPT; ++k) {
+          if (xdst[k] < 0) continue;
+#pragma unroll
+          for (int i = 0; i < M; ++i) prefetch_l1(xsrc[k] + znext + i * plane + xl[k]);
+        }
+      }
+    }
     // y-pass on the TX x TY xy-faces, accumulated grade by grade
 #pragma unroll
     for (int k = 0; k < YPT; ++k) {
