@@ -15,13 +15,14 @@
 
 namespace hermite {
 
-// Tile shapes of the batched kernel per order (NT = 256 threads for all).
-// At m = 3 the 8 x 2 tile gives every thread exactly 3 x-pass, 2 y-pass and
-// 1 z-pass items (a 4 x 4 tile left a partial third x-pass chunk); m = 1 and
-// 2 cannot split evenly over 256 threads with tiles that divide the grids.
+// Tile shapes of the batched kernel per order (NT = 256 threads for all),
+// chosen so that the x-, y- and z-pass items split over the threads with
+// little left for a last partial chunk: at m = 3, 8 x 2 gives exactly 3, 2
+// and 1 items per thread; at m = 1, 16 x 8 gives 4.5, 4 and 2 (8 x 8: 2.25,
+// 2, 1); at m = 2, 16 x 4 gives 5.6, 4.5 and 2.25 (8 x 4: 2.8, 2.25, 1.1).
 template <int M> struct BatchTile;
-template <> struct BatchTile<2> { static constexpr int TX = 8, TY = 8; };
-template <> struct BatchTile<3> { static constexpr int TX = 8, TY = 4; };
+template <> struct BatchTile<2> { static constexpr int TX = 16, TY = 8; };
+template <> struct BatchTile<3> { static constexpr int TX = 16, TY = 4; };
 template <> struct BatchTile<4> { static constexpr int TX = 8, TY = 2; };
 constexpr int kBatchThreads = 256;
 // Resident CTAs per SM the compiler must fit the batched kernel's registers to.
