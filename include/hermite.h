@@ -92,6 +92,9 @@ enum hermite_variant { HERMITE_AUTO = 0, HERMITE_FUSED = 1, HERMITE_SPLIT = 2 };
  * (max_k c*(dt/2)/h_k <= hermite_stability_limit(m)) and builds the 1-D
  * operator tables in exact rational arithmetic on the host.  No GPU work and
  * no device allocation happen here, so a plan can be made without a GPU.
+ * grid[k] (nodes along x1, x2, x3, periodic) runs from 1 to 2^20, with
+ * grid[0] * grid[1] < 2^31 (EINVAL otherwise; the same bounds hold for
+ * hermite_adv_plan and every simulation of a batched plan).
  * Returns EINVAL, EUNSTABLE, EUNSUPPORTED or ENOMEM; *out is NULL on failure. */
 int hermite_plan(hermite_plan_t *out, int m, const int grid[3], const double h[3], double c,
                  double dt, int prec, int state_dtype, int variant);

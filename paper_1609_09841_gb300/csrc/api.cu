@@ -40,6 +40,10 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 namespace {
 
+// Largest x1-x2 plane of a plan: the kernels index nodes within a plane with
+// 32-bit offsets (plane offsets and field strides are 64-bit).
+constexpr long long kMaxPlaneNodes = (1LL << 31) - 1;
+
 // Stability limit of c*tau/h per order m and Taylor order q: the first step
 // at which the largest spectral radius of the Fourier symbol of the isotropic
 // half step, over a 7^3 grid of theta in [0, pi]^3, exceeds 1 + 1e-10
@@ -382,6 +386,9 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
     if (grid[k] < 1 || grid[k] > (1 << 20)) return fail(HERMITE_EINVAL, "grid[%d] = %d out of range", k, grid[k]);
     if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(HERMITE_EINVAL, "h[%d] must be positive", k);
   }
+  if ((long long)grid[0] * grid[1] > kMaxPlaneNodes)
+    return fail(HERMITE_EINVAL, "grid[0]*grid[1] = %lld nodes per x3-plane, above %lld", (long long)grid[0] * grid[1],
+                kMaxPlaneNodes);
   if (!(c > 0.0) || !std::isfinite(c)) return fail(HERMITE_EINVAL, "wave speed c must be positive");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
   if (prec != HERMITE_FP64 && prec != HERMITE_FP32 && prec != HERMITE_HYBRID64 && prec != HERMITE_HYBRIDDF)
@@ -443,6 +450,9 @@ int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double
     if (!(h[k] > 0.0) || !std::isfinite(h[k])) return fail(HERMITE_EINVAL, "h[%d] must be positive", k);
     if (!std::isfinite(a[k])) return fail(HERMITE_EINVAL, "velocity a[%d] is not finite", k);
   }
+  if ((long long)grid[0] * grid[1] > kMaxPlaneNodes)
+    return fail(HERMITE_EINVAL, "grid[0]*grid[1] = %lld nodes per x3-plane, above %lld", (long long)grid[0] * grid[1],
+                kMaxPlaneNodes);
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
   const int qfull = 3 * (2 * m + 1);
   if (q == 0) q = qfull;

@@ -461,6 +461,7 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
     attr_set = true;
   }
   if (zchunk <= 0) zchunk = 16;
+  zchunk = clamp_zchunk(g.zhi - g.zlo, zchunk);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
   dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
   PackedFor<TC> pc{};

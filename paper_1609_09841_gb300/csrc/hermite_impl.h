@@ -81,6 +81,14 @@ struct Geom {
   int zlo, zhi;  // output z layers [zlo, zhi) computed by a launch (the fused and hybrid kernels)
 };
 
+// Cells per CTA along x3 such that ceil(nzl / zchunk) CTAs fit gridDim.y
+// (and gridDim.z), at most 65535: the requested chunk, or a larger one.
+inline int clamp_zchunk(int nzl, int zchunk) {
+  if (zchunk < 1) zchunk = 1;
+  if (nzl > 0 && (nzl + zchunk - 1) / zchunk > 65535) zchunk = (nzl + 65534) / 65535;
+  return zchunk;
+}
+
 // Launch configuration of the fused kernel (chosen per m and precision).
 struct FusedLaunch {
   int zchunk;  // cells per CTA along x3

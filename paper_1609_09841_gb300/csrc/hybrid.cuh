@@ -308,6 +308,7 @@ cudaError_t launch_hybrid_cfg(const double *in, double *out, const Geom &g, cons
     attr_set = true;
   }
   if (zchunk <= 0) zchunk = 16;
+  zchunk = clamp_zchunk(g.zhi - g.zlo, zchunk);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
   dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
   kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co);

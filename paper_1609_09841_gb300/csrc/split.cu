@@ -219,7 +219,7 @@ static cudaError_t launch_interp_cfg(const TS *in, TC *ru, const Geom &g, int z0
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int zchunk = 8;
+  const int zchunk = clamp_zchunk(nzl, 8);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
   dim3 grid(tiles, (nzl + zchunk - 1) / zchunk);
   kern<<<grid, NT, Sh::SMEM, st>>>(in, ru, g, z0, nzl, zchunk, co);

@@ -30,6 +30,7 @@ def _adv(capi, m=2, grid=(8, 8, 8), h=None, a=(1.0, 1.0, 1.0), dt=None, q=0, pre
     (dict(a=(1.0, float("nan"), 0.0)), -1), (dict(dt=0.0), -1), (dict(q=-1), -1), (dict(q=16), -1),
     (dict(prec=2), -4), (dict(prec=3), -4), (dict(prec=0, state=1), -4), (dict(variant=7), -1),
     (dict(q=8, variant=1), -4), (dict(dt=1.0), -5), (dict(q=1), -5),
+    (dict(grid=(1 << 20, 1 << 11, 1)), -1),    # 2^31 nodes in one x1-x2 plane
 ])
 def test_adv_plan_rejects(capi, kw, code):
     rc, p = _adv(capi, **kw)

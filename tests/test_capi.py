@@ -52,12 +52,22 @@ def _plan(capi, m=1, grid=(8, 8, 8), h=None, c=1.0, dt=None, prec=0, state=0, va
     (dict(m=0), -1), (dict(m=4), -1), (dict(grid=(0, 4, 4)), -1), (dict(h=(0.1, -0.1, 0.1)), -1),
     (dict(c=0.0), -1), (dict(dt=0.0), -1), (dict(prec=7), -4), (dict(state=5), -1),
     (dict(prec=0, state=1), -4), (dict(variant=9), -1), (dict(dt=1.0), -5),
+    (dict(grid=((1 << 20) + 1, 2, 2)), -1),
+    (dict(grid=(1 << 20, 1 << 11, 1)), -1),    # 2^31 nodes in one x1-x2 plane: 32-bit in-plane offsets
 ])
 def test_plan_rejects_bad_arguments(capi, kw, code):
     rc, p = _plan(capi, **kw)
     assert rc == code, capi.last_error()
     assert not p.value
     assert capi.last_error()
+
+
+def test_plan_accepts_the_largest_plane(capi):
+    """grid[0] * grid[1] = 2^31 - 2^20 nodes is below the limit; the plan
+    allocates nothing on the device, so this needs no GPU."""
+    rc, p = _plan(capi, grid=(1 << 20, (1 << 11) - 1, 1))
+    assert rc == 0, capi.last_error()
+    capi.lib.hermite_destroy(p)
 
 
 def test_plan_accepts_and_reports_sizes(capi):
