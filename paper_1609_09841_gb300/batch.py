@@ -49,9 +49,11 @@ class BatchPlan:
     def _ptrs(self, xs):
         if len(xs) != len(self):
             raise ValueError("one state per simulation")
+        dt = "float64" if self.state == "fp64" else "float32"
         for i, x in enumerate(xs):
-            if tuple(x.shape) != self.shape(i) or not x.is_cuda or not x.is_contiguous():
-                raise ValueError(f"state {i}: expected contiguous device tensor of shape {self.shape(i)}")
+            if (tuple(x.shape) != self.shape(i) or not x.is_cuda or not x.is_contiguous()
+                    or str(x.dtype).replace("torch.", "") != dt):
+                raise ValueError(f"state {i}: expected contiguous {dt} device tensor of shape {self.shape(i)}")
         return (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
 
     def step(self, ins, outs, parity, stream=None):

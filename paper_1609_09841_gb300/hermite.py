@@ -33,6 +33,27 @@ def _ptr(x):
     return x.data_ptr(), x.is_cuda
 
 
+def _is_fp64(x):
+    """True for a float64 array or tensor, False for float32; anything else
+    is rejected (the library reads exactly the plan's element type, so a
+    buffer of another type would be read out of its bounds or misread)."""
+    name = str(x.dtype).replace("torch.", "")
+    if name == "float64":
+        return True
+    if name == "float32":
+        return False
+    raise ValueError(f"dtype {x.dtype}: expected float32 or float64")
+
+
+def _need(x, dtype, count, what):
+    """A contiguous device tensor of `dtype` (a torch dtype name) with at
+    least `count` elements."""
+    if str(x.dtype).replace("torch.", "") != dtype or not getattr(x, "is_cuda", False) or not x.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous {dtype} device tensor")
+    if x.numel() < count:
+        raise ValueError(f"{what}: {x.numel()} elements, {count} needed")
+
+
 def _stream(stream):
     if stream is not None:
         return ctypes.c_void_p(int(stream))
@@ -99,9 +120,12 @@ class Plan:
         return np.array(out).reshape(P, P)
 
     def _check(self, *xs):
+        """Every x is a state of this plan: its shape and its element type."""
         for x in xs:
             if tuple(x.shape) != self.shape:
                 raise ValueError(f"state shape {tuple(x.shape)} != {self.shape}")
+            if _is_fp64(x) != (self.state == "fp64"):
+                raise ValueError(f"state dtype {x.dtype} does not match the plan's {self.state} state")
 
     def step(self, x_in, x_out, parity, stream=None):
         """x_out = S_parity(x_in) (device tensors: enqueued; host arrays: synchronous)."""
@@ -137,6 +161,8 @@ class Plan:
     def record(self, x, idx, out, stream=None):
         """out[k] (FP64 device) = value of u at flat node idx[k] (int64 device)."""
         self._check(x)
+        _need(idx, "int64", 0, "receiver indices")
+        _need(out, "float64", idx.numel(), "receiver values")
         capi.check(capi.lib.hermite_record(self.handle, ctypes.c_void_p(_ptr(x)[0]), ctypes.c_void_p(idx.data_ptr()),
                                            int(idx.numel()), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
@@ -144,13 +170,17 @@ class Plan:
     def inject(self, adj, idx, w, stream=None):
         """adj[u value at idx[k]] += w[k] (the transpose of record)."""
         self._check(adj)
+        _need(idx, "int64", 0, "receiver indices")
+        _need(w, "float64", idx.numel(), "receiver weights")
         capi.check(capi.lib.hermite_inject(self.handle, ctypes.c_void_p(_ptr(adj)[0]), ctypes.c_void_p(idx.data_ptr()),
                                            int(idx.numel()), ctypes.c_void_p(w.data_ptr()), _stream(stream)))
         return adj
 
     def error(self, x, ref, mask=0b111, stream=None):
         """(max_abs, max_rel, rms, l2_rel) of x - ref (ref FP64, device tensors)."""
-        self._check(x, ref)
+        self._check(x)
+        if tuple(ref.shape) != self.shape or not _is_fp64(ref):
+            raise ValueError(f"ref must be a float64 state of shape {self.shape}")
         out = (ctypes.c_double * 4)()
         rc = capi.lib.hermite_error(self.handle, ctypes.c_void_p(_ptr(x)[0]), ctypes.c_void_p(_ptr(ref)[0]),
                                     int(mask), out, _stream(stream))
