@@ -31,7 +31,10 @@
  *               fastest: the tensor u[m3][m2][m1][n3][n2][n1] of Sec. 3.1 for
  *               each field).  Element type: double for HERMITE_STATE_FP64,
  *               float for HERMITE_STATE_FP32.  Buffers are contiguous and owned
- *               by the caller; device buffers must be 16-byte aligned.
+ *               by the caller; device buffers must be 16-byte aligned.  The
+ *               library cannot see a buffer's size or type: one smaller than
+ *               the state, or of the other element type, is read or written
+ *               past its end.  The Python binding checks both before the call.
  *   parity      0: the input lives on the primal grid (node i at i*h) and the
  *               output on the dual grid (node i at (i+1/2)*h, the centre of the
  *               cell with primal corners i, i+1); 1: dual -> primal (primal node
