@@ -96,7 +96,7 @@ __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
   const int z0 = it.z0, z1 = min(it.z0 + sm.zchunk, g.nz);
-  fused_tile<TS, TC, M, TX, TY, kBatchThreads, 2, kBatchPacked<TC>, kBatchPacked<TC> ? 1 : 0>(
+  fused_tile<TS, TC, M, TX, TY, kBatchThreads, 2, kBatchPacked<TC>, kBatchPacked<TC>>(
       (const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sY, pc);
 }
 

@@ -74,14 +74,4 @@ __device__ __forceinline__ df32 df_mad1(float c, df32 x, df32 acc) {
   return {s.hi, s.lo + (acc.lo + e)};
 }
 
-// acc + c * x, renormalised
-__device__ __forceinline__ df32 df_fma(df32 c, df32 x, df32 acc) {
-  const float p = c.hi * x.hi;
-  float e = fmaf(c.hi, x.hi, -p);
-  e = fmaf(c.hi, x.lo, e);
-  e = fmaf(c.lo, x.hi, e);
-  const df32 s = df_two_sum(acc.hi, p);
-  return df_fast_two_sum(s.hi, s.lo + (acc.lo + e));
-}
-
 }  // namespace hermite

@@ -38,7 +38,6 @@ namespace hermite {
 // L1 prefetch hint (PTX prefetch.global.L1): fetches the line holding p into
 // L1 without a register result.  Callers pass addresses they later load.
 __device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // G: largest total grade the kernel carries (2 for the 4-term series of RK4;
 // 2m for longer series, whose higher grades the z-pass tables fold in).
@@ -101,10 +100,10 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // put a __syncthreads() between the calls).
 // PK: FP32 passes with fma.rn.f32x2 on the packed tables `pc` (kernel
 // parameters); bitwise the same results as the scalar FMAs.
-// PF: prefetch the next plane's x-pass lines during the y- and z-passes,
-// into L1 (1) or L2 (2); 0: none.  The batched kernel uses L1; the
-// single-grid kernels measured slower with either and use none.
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, int PF = 0>
+// PF: prefetch the next plane's x-pass lines into L1 during the y- and
+// z-passes.  The batched kernel uses it; the single-grid kernels measured
+// slower with it (and with the same hint into L2) and do not.
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, bool PF = false>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
                                            TC *__restrict__ sX, TC *__restrict__ sY,
@@ -239,7 +238,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
       }
     }
     __syncthreads();
-    if constexpr (PF != 0) {
+    if constexpr (PF) {
       // the next plane's x-pass lines into L1 while this plane's y- and
       // z-passes run (the left nodes cover all but one x-node per row)
       if (p < z1 - z0) {
@@ -248,12 +247,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         for (int k = 0; k < XPT; ++k) {
           if (xdst[k] < 0) continue;
 #pragma unroll
-          for (int i = 0; i < M; ++i) {
-            if constexpr (PF == 1)
-              prefetch_l1(xsrc[k] + znext + i * plane + xl[k]);
-            else
-              prefetch_l2(xsrc[k] + znext + i * plane + xl[k]);
-          }
+          for (int i = 0; i < M; ++i) prefetch_l1(xsrc[k] + znext + i * plane + xl[k]);
         }
       }
     }

@@ -89,11 +89,6 @@ inline int clamp_zchunk(int nzl, int zchunk) {
   return zchunk;
 }
 
-// Launch configuration of the fused kernel (chosen per m and precision).
-struct FusedLaunch {
-  int zchunk;  // cells per CTA along x3
-};
-
 enum StateKind { kF64 = 0, kF32 = 1 };
 
 // Fused half step (forward or adjoint: the adjoint is the same kernel with

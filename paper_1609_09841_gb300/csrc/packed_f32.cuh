@@ -1,5 +1,5 @@
 // Packed FP32 pairs for the f32x2 instructions of sm_100 and later: a 64-bit
-// register pair holds two floats (lane 0 the low word), and add/mul/fma
+// register pair holds two floats (lane 0 the low word), and mul/fma
 // .rn.f32x2 perform the two lane-wise .rn.f32 operations in one instruction,
 // with the same rounding as the scalar ones.
 #pragma once
