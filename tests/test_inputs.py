@@ -86,3 +86,21 @@ def test_standing_mode_derivatives_are_the_symbolic_ones():
                     want = _sympy_scaled(f, (x, y, z), node, h, (i1, i2, i3))
                     got = S[0, i3, i2, i1, node_idx[2], node_idx[1], node_idx[0]]
                     assert abs(got - want) <= 1e-12, ((i1, i2, i3), node, got, want)
+
+
+@pytest.mark.parametrize("grid", [0, 1])
+def test_advection_plane_wave_derivatives_are_the_symbolic_ones(grid):
+    """The one-field plane wave sin(2 pi k . x + phase) of the advection tests,
+    on the primal and the dual grid (nodes at (i + 1/2) h), against SymPy."""
+    sympy = pytest.importorskip("sympy")
+    m, n, h, k, phase = 3, (4, 3, 5), (1 / 4, 1 / 3, 1 / 5), (1, 2, 1), 0.4
+    x, y, z = sympy.symbols("x y z")
+    f = sympy.sin(2 * sympy.pi * (k[0] * x + k[1] * y + k[2] * z) + sympy.Rational(2, 5))
+    A = HI.plane_wave(m, n, h, k, phase, grid)
+    off = 0.5 if grid else 0.0
+    for node_idx in ((0, 0, 0), (3, 2, 4), (1, 1, 2)):
+        node = tuple((node_idx[d] + off) * h[d] for d in range(3))
+        for i in ((0, 0, 0), (1, 0, 2), (3, 1, 0), (2, 3, 3)):
+            want = _sympy_scaled(f, (x, y, z), node, h, i)
+            got = A[i[2], i[1], i[0], node_idx[2], node_idx[1], node_idx[0]]
+            assert abs(got - want) <= 1e-12, (i, node, got, want)
