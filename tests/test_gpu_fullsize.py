@@ -76,14 +76,18 @@ def test_config2_size_fp64_sampled(torch_cuda, variant):
     _sampled_parity(torch, plan, m, n, h, 1.0, dt, torch.float64, 1e-12)
 
 
-@pytest.mark.parametrize("state", ["fp32", "fp64"])
-def test_metric_size_fp32_sampled(torch_cuda, state):
+@pytest.mark.parametrize("state,schedule", [("fp32", None), ("fp64", None), ("fp32", (5, 64)), ("fp64", (5, 64))])
+def test_metric_size_fp32_sampled(torch_cuda, state, schedule):
     """m = 3, 256^3 (the throughput workload) with FP32 arithmetic; the sample
-    is compared with the FP64 oracle on the same (rounded) input."""
+    is compared with the FP64 oracle on the same (rounded) input.  Schedule
+    (5, 64) is the 8x2-cell, 256-thread tile with z-chunk 64 that the bench's
+    autotuner picks and times at this size."""
     torch = torch_cuda
     from paper_1609_09841_gb300 import Plan
     m, n = 3, (256, 256, 256)
     h = (1 / 256,) * 3
     dt = 0.4 * h[0]
     plan = Plan(m, n, h, 1.0, dt, prec="fp32", state=state)
+    if schedule is not None:
+        plan.set_schedule(*schedule)
     _sampled_parity(torch, plan, m, n, h, 1.0, dt, torch.float32 if state == "fp32" else torch.float64, 2e-5)
