@@ -174,12 +174,8 @@ cudaError_t launch_kron(const TS *in, void *out, const Geom &g, const KronCoeffs
   constexpr size_t smem = S::BYTES;
   static_assert(smem <= 227 * 1024, "shared memory of the tile");
   auto kern = adv_kron_kernel<TS, TC, M, R, TX, TY, NT, WS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
   const int nzc = g.zhi - g.zlo;
   int zc = zchunk < 1 ? 1 : zchunk;
   if ((nzc + zc - 1) / zc > 65535) zc = (nzc + 65534) / 65535;  // gridDim.z limit
@@ -438,12 +434,8 @@ cudaError_t launch_fused_adv(const TS *in, TS *out, const Geom &g, const KronCoe
   static_assert(smem <= 227 * 1024, "shared memory of the tile");
   static_assert(S::NT <= 1024, "threads per CTA");
   auto kern = adv_fused_kernel<TS, TC, M, TX, TY, XC>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
   const int nzc = g.zhi - g.zlo;
   int zc = zchunk < 1 ? 1 : zchunk;
   if ((nzc + zc - 1) / zc > 65535) zc = (nzc + 65534) / 65535;  // gridDim.z limit
@@ -516,12 +508,8 @@ cudaError_t launch_evolve_adv(const TC *ws, TS *out, const Geom &g, int z0, int 
   static_assert(NT <= 1024, "threads per CTA");
   constexpr size_t smem = (size_t)P * P * P * CB * sizeof(TC);
   auto kern = adv_evolve_kernel<TS, TC, M, CB>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
   const size_t ncell = (size_t)nzl * g.ny * g.nx;
   if (ncell == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((ncell + CB - 1) / CB);

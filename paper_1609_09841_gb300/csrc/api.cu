@@ -75,37 +75,6 @@ int check_stable(int m, int q, double c, double tau, const double h[3]) {
   return HERMITE_OK;
 }
 
-size_t state_bytes(const hermite_plan_s *p) {
-  return p->elems * (p->state == HERMITE_STATE_FP64 ? sizeof(double) : sizeof(float));
-}
-
-enum PtrKind { kHostPtr, kDevicePtr, kBadPtr };
-
-PtrKind classify(const void *ptr) {
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return kBadPtr;
-  }
-  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevicePtr;
-  return kHostPtr;
-}
-
-bool overlaps(const void *a, const void *b, size_t bytes) {
-  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-  return x < y + bytes && y < x + bytes;
-}
-
-int check_device_pair(const hermite_plan_s *p, const void *in, void *out) {
-  if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
-  if (overlaps(in, out, state_bytes(p)))
-    return fail(HERMITE_EINVAL, "input and output states overlap (a half step is not in place)");
-  if (((uintptr_t)in | (uintptr_t)out) & 15u)
-    return fail(HERMITE_EINVAL, "device state pointers must be 16-byte aligned");
-  return HERMITE_OK;
-}
-
 Geom geom_of(const hermite_plan_s *p, int s) {
   Geom g;
   g.nx = p->n[0];
@@ -572,10 +541,7 @@ int hermite_adjoint_step(hermite_plan_t p, const void *out_adj, void *in_adj, in
   if (p->eq) return fail(HERMITE_EUNSUPPORTED, "no adjoint for advection plans");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
-  int rc = check_device_pair(p, out_adj, in_adj);
-  if (rc) return rc;
-  if (classify(out_adj) != kDevicePtr || classify(in_adj) != kDevicePtr)
-    return fail(HERMITE_EINVAL, "adjoint steps take device buffers");
+  if (int rc = check_device_only(p, out_adj, in_adj, "hermite_adjoint_step")) return rc;
   return run_step(p, out_adj, in_adj, parity, kAdjoint, (cudaStream_t)stream);
 }
 
@@ -584,10 +550,7 @@ int hermite_step_dc(hermite_plan_t p, const void *in, void *out, int parity, voi
   if (p->eq) return fail(HERMITE_EUNSUPPORTED, "dS/dc is defined for the wave equation only");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan: use hermite_batch_step");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
-  int rc = check_device_pair(p, in, out);
-  if (rc) return rc;
-  if (classify(in) != kDevicePtr || classify(out) != kDevicePtr)
-    return fail(HERMITE_EINVAL, "hermite_step_dc takes device buffers");
+  if (int rc = check_device_only(p, in, out, "hermite_step_dc")) return rc;
   return run_step(p, in, out, parity, kDc, (cudaStream_t)stream);
 }
 

@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
 }
 
 template <typename TS, typename TC>
-static bool &batch_attr_done() {  // dynamic shared memory attribute set for this instantiation
-  static bool done = false;
-  return done;
+static SmemAttrOnce &batch_smem_once() {  // dynamic shared-memory limit raised, per device
+  static SmemAttrOnce once;
+  return once;
 }
 
 template <typename TS, typename TC>
@@ -156,12 +156,9 @@ static cudaError_t launch_batch_t(const BatchSim *sims, const void *coeffs, cons
                                   int *counter, int s, int grid, cudaStream_t st) {
   auto kern = batch_step_kernel<TS, TC>;
   constexpr size_t smem = batch_smem_bytes<TC>() + 16;
-  if (!batch_attr_done<TS, TC>()) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    batch_attr_done<TS, TC>() = true;
-  }
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  cudaError_t e = raise_smem_limit(batch_smem_once<TS, TC>(), kern, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   kern<<<grid, kBatchThreads, smem, st>>>(sims, (const unsigned char *)coeffs, items, nitems, counter, s);
   return cudaGetLastError();
@@ -172,8 +169,7 @@ static int occupancy_t() {
   int blocks = 0;
   constexpr size_t smem = batch_smem_bytes<TC>() + 16;
   auto kern = batch_step_kernel<TS, TC>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
-    batch_attr_done<TS, TC>() = true;
+  if (raise_smem_limit(batch_smem_once<TS, TC>(), kern, smem) != cudaSuccess) cudaGetLastError();
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kBatchThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;

@@ -448,12 +448,8 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
     else
       return fused_step_kernel<TS, TC, M, TX, TY, NT, G>;
   }();
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, Sh::SMEM); e != cudaSuccess) return e;
   if (zchunk <= 0) zchunk = 16;
   zchunk = clamp_zchunk(g.zhi - g.zlo, zchunk);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);

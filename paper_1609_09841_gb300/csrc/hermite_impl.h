@@ -3,12 +3,34 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 
 namespace hermite {
 
 constexpr int kMaxM = 4;  // largest M = m + 1
+constexpr int kMaxDevices = 64;  // device ordinals the per-device records below cover
+
+// Per-device record that a kernel's dynamic shared-memory limit has been
+// raised.  The attribute belongs to each device's context, so a launcher keeps
+// one record per kernel instantiation (a function-local static, zero at load)
+// and raises the limit on every device it first runs on.
+struct SmemAttrOnce {
+  std::atomic<bool> done[kMaxDevices];
+};
+
+template <typename Kern>
+cudaError_t raise_smem_limit(SmemAttrOnce &once, Kern kern, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < kMaxDevices;
+  if (tracked && once.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && tracked) once.done[dev].store(true, std::memory_order_release);
+  return e;
+}
 
 // Tables of the fused half step.  For one cell and one input field the half
 // step is the Kronecker sum  sum_s beta_s sum_{a+b+c=s} Gz_c (x) Gy_b (x) Gx_a

@@ -301,12 +301,8 @@ cudaError_t launch_hybrid_cfg(const double *in, double *out, const Geom &g, cons
                               cudaStream_t st) {
   using Sh = HybridShape<M, TX, TY>;
   auto kern = hybrid_step_kernel<Hi, M, TX, TY, NT>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, Sh::SMEM); e != cudaSuccess) return e;
   if (zchunk <= 0) zchunk = 16;
   zchunk = clamp_zchunk(g.zhi - g.zlo, zchunk);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);

@@ -3,7 +3,10 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <string>
+
+#include "../../include/hermite.h"
 
 #include "advect.h"
 #include "hermite_impl.h"
@@ -46,3 +49,54 @@ struct hermite_plan_s {
   cudaStream_t copy_in = nullptr, copy_out = nullptr;  // host-buffer steps: copy streams
   cudaEvent_t ev[2 * 16 + 2] = {};                     // host-buffer steps: chunk events
 };
+
+namespace hermite {
+
+// Argument checks on state buffers, shared by every entry point that takes
+// them, so that a host pointer never reaches a kernel.
+
+inline size_t state_bytes(const hermite_plan_s *p) {
+  return p->elems * (p->state == HERMITE_STATE_FP64 ? sizeof(double) : sizeof(float));
+}
+
+enum PtrKind { kHostPtr, kDevicePtr, kBadPtr };
+
+// Where a pointer lives: device (or managed) memory, host memory (pageable
+// or pinned), or unknown to the runtime (no device, or the query failed).
+inline PtrKind classify(const void *ptr) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return kBadPtr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kDevicePtr;
+  return kHostPtr;
+}
+
+inline bool overlaps(const void *a, const void *b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+// Non-null, non-overlapping, 16-byte aligned (EINVAL otherwise).
+inline int check_device_pair(const hermite_plan_s *p, const void *in, void *out) {
+  if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
+  if (overlaps(in, out, state_bytes(p)))
+    return fail(HERMITE_EINVAL, "input and output states overlap (a half step is not in place)");
+  if (((uintptr_t)in | (uintptr_t)out) & 15u)
+    return fail(HERMITE_EINVAL, "device state pointers must be 16-byte aligned");
+  return HERMITE_OK;
+}
+
+// check_device_pair, and both buffers in device memory (EINVAL for host
+// buffers, ECUDA when the runtime cannot tell).  `what` names the call.
+inline int check_device_only(const hermite_plan_s *p, const void *in, void *out, const char *what) {
+  if (int rc = check_device_pair(p, in, out)) return rc;
+  const PtrKind ki = classify(in), ko = classify(out);
+  if (ki == kBadPtr || ko == kBadPtr) return fail(HERMITE_ECUDA, "cannot query pointer attributes (no CUDA device?)");
+  if (ki != kDevicePtr || ko != kDevicePtr) return fail(HERMITE_EINVAL, "%s takes device buffers", what);
+  return HERMITE_OK;
+}
+
+}  // namespace hermite

@@ -213,12 +213,8 @@ static cudaError_t launch_interp_cfg(const TS *in, TC *ru, const Geom &g, int z0
                                      const InterpCoeffs<TC> &co, cudaStream_t st) {
   using Sh = InterpShape<TC, M, TX, TY>;
   auto kern = interp_kernel<TS, TC, M, TX, TY, NT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, Sh::SMEM); e != cudaSuccess) return e;
   const int zchunk = clamp_zchunk(nzl, 8);
   const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
   dim3 grid(tiles, (nzl + zchunk - 1) / zchunk);
@@ -231,12 +227,8 @@ static cudaError_t launch_evolve_cfg(const TC *ru, TS *out, const Geom &g, int z
                                      const EvolveParams &ep, cudaStream_t st) {
   constexpr size_t smem = (size_t)5 * CB * (2 * M) * (2 * M) * (2 * M) * sizeof(TC);
   auto kern = evolve_kernel<TS, TC, M, CB, NT>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
   const size_t cells = (size_t)g.nx * g.ny * nzl;
   dim3 grid((unsigned)((cells + CB - 1) / CB));
   kern<<<grid, NT, smem, st>>>(ru, out, g, z0, nzl, ep);

@@ -28,7 +28,6 @@ constexpr size_t kStaticBytes = HERMITE_STATIC_WORKSPACE_BYTES;
 // with cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_split_ws[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
 std::atomic<void *> g_ws_addr[kMaxDevices];
 std::mutex g_ws_mutex;
 
@@ -67,13 +66,9 @@ int hermite_step_split_static(hermite_plan_t p, const void *in, void *out, int p
   if (!p || p->batch) return fail(HERMITE_EINVAL, "plan is NULL or batched");
   if (p->eq) return fail(HERMITE_EUNSUPPORTED, "the allocation-free step is for wave-equation plans");
   if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
-  if (!in || !out) return fail(HERMITE_EINVAL, "null state pointer");
   if (p->prec != HERMITE_FP64 && p->prec != HERMITE_FP32)
     return fail(HERMITE_EUNSUPPORTED, "the split kernels have no hybrid precision");
-  const size_t bytes = p->elems * (p->state == HERMITE_STATE_FP64 ? 8 : 4);
-  const uintptr_t x = (uintptr_t)in, y = (uintptr_t)out;
-  if (x < y + bytes && y < x + bytes) return fail(HERMITE_EINVAL, "input and output states overlap");
-  if ((x | y) & 15u) return fail(HERMITE_EINVAL, "device state pointers must be 16-byte aligned");
+  if (int rc = check_device_only(p, in, out, "hermite_step_split_static")) return rc;
   const int P = 2 * p->m + 2;
   const size_t elt = p->prec == HERMITE_FP64 ? sizeof(double) : sizeof(float);
   const size_t per_layer = (size_t)2 * P * P * P * p->n[0] * p->n[1] * elt;

@@ -56,7 +56,7 @@ def test_static_workspace_step_matches_hermite_step(torch_cuda, m, n, prec, stat
 def test_static_workspace_rejects_oversized_layer(torch_cuda):
     torch = torch_cuda
     from paper_1609_09841_gb300 import Plan, capi
-    n = (64, 64, 4)           # one layer of m = 3 FP64 polynomials: 64 MiB > 16 MiB
+    n = (64, 64, 4)           # one layer of m = 3 FP64 polynomials: 2*8^3*64*64*8 B = 32 MiB > 16 MiB
     h = tuple(1.0 / v for v in n)
     plan = Plan(3, n, h, 1.0, 0.4 * min(h))
     x = plan.empty()
@@ -66,3 +66,21 @@ def test_static_workspace_rejects_oversized_layer(torch_cuda):
     assert rc == capi.HERMITE_EINVAL
     msg = capi.last_error()
     assert "static workspace" in msg and str(capi.lib.hermite_static_workspace_bytes()) in msg
+
+
+def test_static_workspace_rejects_host_buffers(torch_cuda):
+    """Host buffers are refused before any launch, as hermite_step's device-only
+    calls refuse them: a kernel given a host address would fault."""
+    from paper_1609_09841_gb300 import Plan, capi
+    n = (8, 8, 8)
+    h = tuple(1.0 / v for v in n)
+    plan = Plan(1, n, h, 1.0, 0.4 * min(h))
+    x = np.zeros(plan.elems)
+    y = np.zeros(plan.elems)
+    dev = plan.empty()
+    for a, b in ((x, y), (dev, y), (x, dev)):
+        pa = a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+        pb = b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr()
+        rc = capi.lib.hermite_step_split_static(plan.handle, ctypes.c_void_p(pa), ctypes.c_void_p(pb), 0, None)
+        assert rc == capi.HERMITE_EINVAL, capi.last_error()
+        assert "device buffers" in capi.last_error()
