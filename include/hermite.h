@@ -78,7 +78,15 @@ enum hermite_prec {
   HERMITE_HYBRID64 = 2, /* FP64 state; every contraction applied to grade-0 data (the node data,
                            the x- and y-interpolants) in FP64, the rest (small grade >= 1 terms of
                            the Taylor series) in FP32.  Fused variant only. */
-  HERMITE_HYBRIDDF = 3  /* as HYBRID64 with the FP64 part in double-float (pairs of FP32) */
+  HERMITE_HYBRIDDF = 3, /* as HYBRID64 with the FP64 part in double-float (pairs of FP32) */
+  /* FP32 x- and y-passes; the z-pass (the mode product along x3 of the 1-D
+     evolution-and-truncation factors, Sec. 3.1 Alg. 1/2 with Sec. 3.2's
+     evolution folded in) on the tensor cores (tcgen05) with FP32 accumulation,
+     its operands split into pieces of the tensor-core input type.  State FP32
+     or FP64 (loaded, computed, stored back).  Fused variant, RK4 (q = 4),
+     single-grid plans only. */
+  HERMITE_3XTF32 = 4,   /* y = a1 + a2 (TF32 pieces); a1 b1 + a1 b2 + a2 b1 */
+  HERMITE_SPLITBF16 = 5 /* y = a1 + a2 + a3 (BF16 pieces); the six products of total order <= 2 */
 };
 
 enum hermite_state_type { HERMITE_STATE_FP64 = 0, HERMITE_STATE_FP32 = 1 };
@@ -158,6 +166,15 @@ int hermite_record(hermite_plan_t plan, const void *state, const long long *idx,
                    double *out, void *stream);
 int hermite_inject(hermite_plan_t plan, void *adj_state, const long long *idx, int count,
                    const double *w, void *stream);
+
+/* Device status of the plan's kernels: *status receives the OR of the flags
+ * that kernels raised since the last call (0: none) and the flags are
+ * cleared.  Bit 0: a CTA of the tensor-core kernel (HERMITE_3XTF32,
+ * HERMITE_SPLITBF16) gave up waiting for its MMAs after its bounded wait; its
+ * outputs are then incomplete.  Synchronises `stream`.  The word is allocated
+ * by the first tensor-core step of the plan; make that step outside any stream
+ * capture. */
+int hermite_device_status(hermite_plan_t plan, int *status, void *stream);
 
 /* Kernel schedule of the fused half step: `tile` picks one of
  * hermite_schedule_count(plan) compiled tile shapes (cells per CTA in x1, x2

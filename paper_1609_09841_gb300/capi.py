@@ -23,6 +23,8 @@ HERMITE_FP64 = 0
 HERMITE_FP32 = 1
 HERMITE_HYBRID64 = 2
 HERMITE_HYBRIDDF = 3
+HERMITE_3XTF32 = 4
+HERMITE_SPLITBF16 = 5
 HERMITE_STATE_FP64 = 0
 HERMITE_STATE_FP32 = 1
 HERMITE_AUTO = 0
@@ -77,6 +79,7 @@ def _load():
         "hermite_batch_run": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "hermite_set_schedule": (I, [P, I, I]),
         "hermite_dot": (I, [P, P, P, DP, P]),
+        "hermite_device_status": (I, [P, IP, P]),
         "hermite_record": (I, [P, P, P, I, P, P]),
         "hermite_inject": (I, [P, P, P, I, P, P]),
         "hermite_last_error": (ctypes.c_char_p, []),

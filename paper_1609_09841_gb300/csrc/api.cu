@@ -197,6 +197,23 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     }
     const StepCoeffs<double> &cd = mode == kAdjoint ? p->adj : (mode == kDc ? p->dc : p->fwd);
     const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
+    if (is_tc_prec(p->prec)) {
+      if (!p->status) {
+        cudaError_t ea = cudaMalloc(&p->status, sizeof(int));
+        if (ea != cudaSuccess) {
+          cudaGetLastError();
+          p->status = nullptr;
+          return fail(HERMITE_ENOMEM, "device status word");
+        }
+        ea = cudaMemset(p->status, 0, sizeof(int));
+        if (ea != cudaSuccess) return cuda_fail(ea, "device status word");
+      }
+      const TcBTable &bt = mode == kAdjoint ? p->tc_adj : (mode == kDc ? p->tc_dc : p->tc_fwd);
+      e = launch_fused_tc(p->prec == HERMITE_3XTF32 ? 0 : 1, p->m, p->state == HERMITE_STATE_FP64 ? kF64 : kF32, in,
+                          out, g, cf, bt, p->zchunk, p->status, st);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core half-step launch");
+      return HERMITE_OK;
+    }
     const bool rk4 = p->q == 4;  // longer series run the kernels with more grades
     if (p->prec == HERMITE_FP64)
       e = rk4 ? launch_fused_f64(p->m, p->tile, (const double *)in, (double *)out, g, cd, p->zchunk, st)
@@ -327,6 +344,12 @@ void build_tables(hermite_plan_s *p) {
     for (size_t q = 0; q < sizeof(StepCoeffs<double>) / sizeof(double); ++q) r[q] -= (double)hi[q];
     dsts[k]->lo = cast_coeffs<float>(rest);
   }
+  if (is_tc_prec(p->prec)) {
+    const int kind = p->prec == HERMITE_3XTF32 ? 0 : 1;
+    p->tc_fwd = build_tc_btable(p->m, kind, p->fwd);
+    p->tc_adj = build_tc_btable(p->m, kind, p->adj);
+    p->tc_dc = build_tc_btable(p->m, kind, p->dc);
+  }
 }
 
 }  // namespace
@@ -360,20 +383,23 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
                 kMaxPlaneNodes);
   if (!(c > 0.0) || !std::isfinite(c)) return fail(HERMITE_EINVAL, "wave speed c must be positive");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
-  if (prec != HERMITE_FP64 && prec != HERMITE_FP32 && prec != HERMITE_HYBRID64 && prec != HERMITE_HYBRIDDF)
+  if (prec != HERMITE_FP64 && prec != HERMITE_FP32 && prec != HERMITE_HYBRID64 && prec != HERMITE_HYBRIDDF &&
+      !is_tc_prec(prec))
     return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
   if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
     return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
-  if (prec != HERMITE_FP32 && state_dtype != HERMITE_STATE_FP64)
+  if (prec != HERMITE_FP32 && !is_tc_prec(prec) && state_dtype != HERMITE_STATE_FP64)
     return fail(HERMITE_EUNSUPPORTED, "FP64 and hybrid arithmetic need an FP64 state");
+  if (is_tc_prec(prec) && variant == HERMITE_SPLIT)
+    return fail(HERMITE_EUNSUPPORTED, "the tensor-core precisions run the fused kernel only");
   if (variant != HERMITE_AUTO && variant != HERMITE_FUSED && variant != HERMITE_SPLIT)
     return fail(HERMITE_EINVAL, "variant %d unknown", variant);
   if (variant == HERMITE_SPLIT && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
     return fail(HERMITE_EUNSUPPORTED, "the split variant has no hybrid precision");
   if (q < 4 || q > 3 * (2 * m + 1))
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * m + 1), m);
-  if (q != 4 && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
-    return fail(HERMITE_EUNSUPPORTED, "the hybrid precisions run the 4-stage series only");
+  if (q != 4 && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF || is_tc_prec(prec)))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid and tensor-core precisions run the 4-stage series only");
   const double tau = 0.5 * dt;
   if (int rc = check_stable(m, q, c, tau, h)) return rc;
   const size_t nodes = (size_t)grid[0] * grid[1] * grid[2];
@@ -483,8 +509,8 @@ int hermite_set_taylor_order(hermite_plan_t p, int q) {
   if (p->eq) return fail(HERMITE_EUNSUPPORTED, "advection plans fix q at hermite_adv_plan");
   if (q < 4 || q > 3 * (2 * p->m + 1))
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * p->m + 1), p->m);
-  if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF))
-    return fail(HERMITE_EUNSUPPORTED, "the hybrid precisions run the 4-stage series only");
+  if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF || is_tc_prec(p->prec)))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid and tensor-core precisions run the 4-stage series only");
   if (int rc = check_stable(p->m, q, p->c, p->tau, p->h)) return rc;
   p->q = q;
   p->evolve.q = q;
@@ -500,6 +526,7 @@ int hermite_schedule_count(hermite_plan_t p) {
   if (!p || p->batch) return 0;
   if (p->eq) return p->variant == HERMITE_SPLIT ? 1 : kAdvFusedTiles;
   if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
+  if (is_tc_prec(p->prec)) return 1;
   return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
 }
 
@@ -606,6 +633,20 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
   return HERMITE_OK;
 }
 
+int hermite_device_status(hermite_plan_t p, int *status, void *stream) {
+  if (!p || !status) return fail(HERMITE_EINVAL, "null argument");
+  *status = 0;
+  if (!p->status) return HERMITE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, p->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device status read");
+  *status = v;
+  return HERMITE_OK;
+}
+
 int hermite_dot(hermite_plan_t p, const void *a, const void *b, double *out, void *stream) {
   if (!p || !a || !b || !out) return fail(HERMITE_EINVAL, "null argument");
   if (p->batch) return fail(HERMITE_EINVAL, "batched plan");
@@ -636,6 +677,7 @@ void hermite_destroy(hermite_plan_t p) {
     if (p->stage[k]) cudaFree(p->stage[k]);
   if (p->red) cudaFree(p->red);
   if (p->red_host) cudaFreeHost(p->red_host);
+  if (p->status) cudaFree(p->status);
   delete p;
 }
 

@@ -88,6 +88,49 @@ inline PackedCoeffs pack_coeffs(const StepCoeffs<float> &c) {
   return p;
 }
 
+// Exact float -> double with integer operations (the hardware widening runs
+// on the FP64 pipe at about 1.5 per clock per SM on GB300, so a kernel that
+// stores an FP64 state from FP32 results would be bound by it).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned s = b & 0x80000000u, a = b & 0x7FFFFFFFu;
+  unsigned hi, lo;
+  if (a >= 0x00800000u && a < 0x7F800000u) {  // normal: rebias the exponent by 1023 - 127
+    hi = s | ((a >> 3) + 0x38000000u);
+    lo = b << 29;
+  } else if (a >= 0x7F800000u) {  // infinity, NaN (payload kept)
+    hi = s | 0x7FF00000u | ((a & 0x7FFFFFu) >> 3);
+    lo = b << 29;
+  } else if (a == 0u) {
+    hi = s;
+    lo = 0u;
+  } else {  // subnormal a * 2^-149: normalise
+    const unsigned lz = __clz(a);          // 9..31
+    const unsigned mm = (a << lz) << 1;    // mantissa without its leading one
+    hi = s | ((905u - lz) << 20) | (mm >> 12);
+    lo = mm << 20;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename TS>
+__device__ __forceinline__ TS state_from_float(float v) {
+  if constexpr (sizeof(TS) == 8)
+    return f2d_exact(v);
+  else
+    return v;
+}
+
+// Conversion of a computed value to the state type: exact, and by integer
+// operations when FP32 results go to an FP64 state.
+template <typename TS, typename TC>
+__device__ __forceinline__ TS to_state(TC v) {
+  if constexpr (sizeof(TS) == 8 && sizeof(TC) == 4)
+    return f2d_exact(v);
+  else
+    return (TS)v;
+}
+
 __device__ __forceinline__ int wrap_index(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
@@ -388,7 +431,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
 #pragma unroll
         for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
-          for (int r = 0; r < M; ++r) o[(size_t)((fo * M + r) * M * M) * plane] = (TS)(zacc[k][fo][r] + (E[fo][r] + O[fo][r]));
+          for (int r = 0; r < M; ++r) o[(size_t)((fo * M + r) * M * M) * plane] = to_state<TS>(zacc[k][fo][r] + (E[fo][r] + O[fo][r]));
       }
 #pragma unroll
       for (int fo = 0; fo < 2; ++fo)

@@ -136,6 +136,20 @@ int hybrid_tile_count();
 cudaError_t launch_hybrid(int kind, int m, int tile, const double *in, double *out, const Geom &g,
                           const HybridCoeffs &co, int zchunk, cudaStream_t st);
 
+// Fused half step with the z-pass on the tensor cores (tcgen05): kind 0 =
+// 3xTF32, kind 1 = BF16 x 3, FP32 accumulation; FP32 (kF32) or FP64 (kF64)
+// state.  The z-pass B operand is built once per plan on the host.  A CTA
+// whose wait for its MMAs gives up sets bit 0 of *status (device int).
+// The z-pass B operand (all pieces, in shared-memory byte order), built on the
+// host from the Kz tables; at most 3 pieces x 16 x 32 BF16 or 2 x 16 x 24 TF32.
+struct TcBTable {
+  uint4 words[192];
+};
+TcBTable build_tc_btable(int m, int kind, const StepCoeffs<double> &co);
+cudaError_t launch_fused_tc(int kind, int m, int state, const void *in, void *out, const Geom &g,
+                            const StepCoeffs<float> &co, const TcBTable &bt, int zchunk, int *status,
+                            cudaStream_t st);
+
 // Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
 // output z-layers [z0, z0 + nzl); evolution reads it and writes the new node
 // data of those layers.

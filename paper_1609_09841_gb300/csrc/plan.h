@@ -29,6 +29,8 @@ struct hermite_plan_s {
   hermite::StepCoeffs<double> fwd, adj, dc;
   hermite::StepCoeffs<float> fwd32, adj32, dc32;
   hermite::HybridCoeffs hyb_fwd, hyb_adj, hyb_dc;
+  hermite::TcBTable tc_fwd, tc_adj, tc_dc;  // tensor-core precisions: z-pass B operands
+  int *status = nullptr;                    // device status word of the tensor-core kernel
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
   int q = 4;                // Taylor stages of the local evolution (4 = RK4)
@@ -91,6 +93,9 @@ inline int check_device_pair(const hermite_plan_s *p, const void *in, void *out)
 
 // check_device_pair, and both buffers in device memory (EINVAL for host
 // buffers, ECUDA when the runtime cannot tell).  `what` names the call.
+// Tensor-core precisions (the z-pass on tcgen05).
+inline bool is_tc_prec(int prec) { return prec == HERMITE_3XTF32 || prec == HERMITE_SPLITBF16; }
+
 inline int check_device_only(const hermite_plan_s *p, const void *in, void *out, const char *what) {
   if (int rc = check_device_pair(p, in, out)) return rc;
   const PtrKind ki = classify(in), ko = classify(out);

@@ -11,7 +11,8 @@ import numpy as np
 from . import capi
 
 PRECISIONS = {"fp64": capi.HERMITE_FP64, "fp32": capi.HERMITE_FP32, "hybrid64": capi.HERMITE_HYBRID64,
-              "hybriddf": capi.HERMITE_HYBRIDDF}
+              "hybriddf": capi.HERMITE_HYBRIDDF, "3xtf32": capi.HERMITE_3XTF32,
+              "splitbf16": capi.HERMITE_SPLITBF16}
 STATES = {"fp64": capi.HERMITE_STATE_FP64, "fp32": capi.HERMITE_STATE_FP32}
 VARIANTS = {"auto": capi.HERMITE_AUTO, "fused": capi.HERMITE_FUSED, "split": capi.HERMITE_SPLIT}
 
@@ -149,6 +150,13 @@ class Plan:
         capi.check(capi.lib.hermite_step_dc(self.handle, ctypes.c_void_p(_ptr(x_in)[0]),
                                             ctypes.c_void_p(_ptr(x_out)[0]), int(parity), _stream(stream)))
         return x_out
+
+    def device_status(self, stream=None):
+        """Flags raised by the plan's kernels since the last call (0: none),
+        then cleared; bit 0: a tensor-core CTA gave up waiting for its MMAs."""
+        out = ctypes.c_int()
+        capi.check(capi.lib.hermite_device_status(self.handle, ctypes.byref(out), _stream(stream)))
+        return out.value
 
     def dot(self, a, b, stream=None):
         """FP64 sum of a * b over every entry of two device states."""
