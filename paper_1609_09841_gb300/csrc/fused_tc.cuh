@@ -62,7 +62,16 @@ struct TcShape {
   static constexpr int APIECE = ROWS * KP * ESZ;         // bytes of one piece of A
   static constexpr int BPIECE = 16 * KP * ESZ;           // bytes of one piece of B
   static constexpr int TMEM_COLS = NTILE * 16 <= 32 ? 32 : 64;
-  static constexpr size_t XBYTES = (size_t)Base::SX * sizeof(float);
+  // x-pass results [f][iz][iy][a][ix'][ey][ex], one block of XB words per (f, iz, iy).  A warp of
+  // y-items spans 8 cells (fx) x 4 iz (below), so that its 4-byte stores of the A pieces fall on
+  // (row % 8) * 4 + k % 4: 32 distinct banks.  Its sX reads then differ by iz * M * XB + fx words,
+  // and the x-items run (ex, ey, iz, iy, f).  For M = 4, XB = 6 modulo 32 puts all three on
+  // distinct banks (M XB = 24 modulo 32 separates the four iz rows of a read, and consecutive
+  // (ex, ey) blocks of a store fall 24 words apart).
+  static constexpr int XB0 = Base::XB0;
+  static constexpr int XB = M == 4 ? XB0 + ((6 - XB0 % 32) + 32) % 32 : Base::XB;
+  static constexpr int SX = 2 * M * M * XB;
+  static constexpr size_t XBYTES = (size_t)SX * sizeof(float);
   static constexpr size_t AOFF = (XBYTES + 127) / 128 * 128;
   static constexpr size_t BOFF = AOFF + (size_t)PIECES * APIECE;
   static constexpr size_t SMEM = BOFF + (size_t)PIECES * BPIECE;
@@ -161,14 +170,14 @@ __global__ void __launch_bounds__(NT, 2)
     int t = e < Sh::XITEMS ? e : 0;
     const int ex = t % TX; t /= TX;
     const int ey = t % NYN; t /= NYN;
-    const int iy = t % M; t /= M;
-    const int iz = t % M;
+    const int iz = t % M; t /= M;       // order (ex, ey, iz, iy, f): see TcShape::XB
+    const int iy = t % M;
     const int f = t / M;
     const int gy = wrap_index(y0 + s + ey, ny);
     xsrc[k] = in + (size_t)(((f * M + iz) * M + iy) * M) * plane;
     xl[k] = gy * nx + wrap_index(x0 + s + ex, nx);
     xr[k] = gy * nx + wrap_index(x0 + s + ex + 1, nx);
-    xdst[k] = e < Sh::XITEMS ? ((f * M + iz) * M + iy) * Sh::XB + ey * TX + ex : -1;
+    xdst[k] = e < Sh::XITEMS ? ((f * M + iz) * M + iy) * T::XB + ey * TX + ex : -1;
   }
   // y-items: base of the two edges in sX; byte offsets of the item's A row
   // (r = 0) and of its K column per grade
@@ -177,19 +186,13 @@ __global__ void __launch_bounds__(NT, 2)
   for (int k = 0; k < YPT; ++k) {
     const int e = threadIdx.x + k * NT;
     int t = e < Sh::YITEMS ? e : 0;
-    int fx, fy, ixp;
-    if constexpr (TX * TY < 32) {
-      fx = t % TX; t /= TX;
-      ixp = t % M; t /= M;
-      fy = t % TY; t /= TY;
-    } else {
-      fx = t % TX; t /= TX;
-      fy = t % TY; t /= TY;
-      ixp = t % M; t /= M;
-    }
-    const int iz = t % M;
+    // item order (fx, iz, fy, ix', f): see TcShape::XB
+    const int fx = t % TX; t /= TX;
+    const int iz = t % M; t /= M;
+    const int fy = t % TY; t /= TY;
+    const int ixp = t % M;
     const int f = t / M;
-    ysrc[k] = e < Sh::YITEMS ? (f * M + iz) * M * Sh::XB + ixp * XS + fy * TX + fx : -1;
+    ysrc[k] = e < Sh::YITEMS ? (f * M + iz) * M * T::XB + ixp * XS + fy * TX + fx : -1;
     const int row0 = ixp * T::NC + fy * TX + fx;  // row of r = 0; r adds r * M * NC
     yrow[k] = row0;
 #pragma unroll
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(NT, 2)
       for (int a = 0; a < NA; ++a)
 #pragma unroll
         for (int iy = 0; iy < M; ++iy) {
-          const TC *xi = sX + ysrc[k] + iy * Sh::XB + a * M * XS;
+          const TC *xi = sX + ysrc[k] + iy * T::XB + a * M * XS;
           const TC L = xi[0], R = xi[TX];
           const TC sv = (iy & 1) ? R - L : R + L;
           const TC dv = (iy & 1) ? R + L : R - L;

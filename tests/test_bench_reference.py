@@ -20,6 +20,10 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.bench_config(1)     # the same workload as our arm's line
+    assert line["metric"] == bench.METRIC and line["steps"] == 1
 
 
 def test_reference_arm_under_torchrun_prints_once():
