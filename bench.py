@@ -50,6 +50,7 @@ VARIANTS = {
     "splitbf16": ("splitbf16", "fp32", "f32 + BF16x3 tensor cores"),
     "fp32_s64": ("fp32", "fp64", "f32"),
     "hybriddf": ("hybriddf", "fp64", "double-float + f32"),
+    "remainder": ("remainder", "fp64", "f32 exact-split + f32"),
     "hybrid64": ("hybrid64", "fp64", "f64 + f32"),
     "fp64": ("fp64", "fp64", "f64"),
 }
@@ -438,12 +439,13 @@ def run_ours(args, rank, world):
     kern = {"fp32": "fused_step_kernel<float, float, ...>", "fp32_s64": "fused_step_kernel<double, float, ...>",
             "3xtf32": "tc_step_kernel<..., 3xTF32>", "splitbf16": "tc_step_kernel<..., BF16x3>",
             "hybriddf": "hybrid_step_kernel<HiDF, ...>", "hybrid64": "hybrid_step_kernel<HiF64, ...>",
+            "remainder": "rem_step_kernel<4, 8, 4, 512>",
             "fp64": "fused_step_kernel<double, double, ...>"}
     cfg = bench_config(world, m, args.side)
     out = {
         "metric": METRIC, "value": hr["value"], "unit": "DOF-updates/s", "n_gpus": world, "steps": hr["steps"],
         "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": arith.split(" ")[0] if head != "hybriddf" else "df32+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"hybriddf": "df32+f32", "remainder": "f32 (exact-split pairs)"}.get(head, arith.split(" ")[0]), "data": "synthetic",
         "config": cfg,
         "headline": {"variant": head, "prec": prec, "state": state, "arithmetic": arith,
                      "t1_max_rel": hr["t1_max_rel"], "bar": BAR, "meets_bar": hr["meets_bar"],

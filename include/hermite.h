@@ -86,7 +86,16 @@ enum hermite_prec {
      or FP64 (loaded, computed, stored back).  Fused variant, RK4 (q = 4),
      single-grid plans only. */
   HERMITE_3XTF32 = 4,   /* y = a1 + a2 (TF32 pieces); a1 b1 + a1 b2 + a2 b1 */
-  HERMITE_SPLITBF16 = 5 /* y = a1 + a2 + a3 (BF16 pieces); the six products of total order <= 2 */
+  HERMITE_SPLITBF16 = 5, /* y = a1 + a2 + a3 (BF16 pieces); the six products of total order <= 2 */
+  /* FP64 state; every 1-D factor applied in the one-sided Taylor-remainder
+     form G_a [L; R] = TS_a L + RR_a (R - T L), which Hermite interpolation's
+     exactness on polynomials of degree <= 2m+1 (Sec. 3.1) allows: T L is the
+     right node's data of the left node's degree-m Taylor polynomial.  The
+     large entries of RR_a then act on the small remainder, in FP32; the
+     remainder and the grade-0 chain (short dyadic coefficients) are exact
+     FP32 sums on a per-item grid.  Fused variant, RK4 (q = 4), forward steps
+     (hermite_step) of single-grid plans. */
+  HERMITE_REMAINDER = 6
 };
 
 enum hermite_state_type { HERMITE_STATE_FP64 = 0, HERMITE_STATE_FP32 = 1 };

@@ -197,6 +197,12 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     }
     const StepCoeffs<double> &cd = mode == kAdjoint ? p->adj : (mode == kDc ? p->dc : p->fwd);
     const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
+    if (p->prec == HERMITE_REMAINDER) {
+      if (mode != kForward) return fail(HERMITE_EUNSUPPORTED, "the remainder-form precision has forward steps only");
+      e = launch_remainder(p->m, (const double *)in, (double *)out, g, p->rem, p->zchunk, st);
+      if (e != cudaSuccess) return cuda_fail(e, "remainder-form half-step launch");
+      return HERMITE_OK;
+    }
     if (is_tc_prec(p->prec)) {
       if (!p->status) {
         cudaError_t ea = cudaMalloc(&p->status, sizeof(int));
@@ -344,6 +350,7 @@ void build_tables(hermite_plan_s *p) {
     for (size_t q = 0; q < sizeof(StepCoeffs<double>) / sizeof(double); ++q) r[q] -= (double)hi[q];
     dsts[k]->lo = cast_coeffs<float>(rest);
   }
+  if (p->prec == HERMITE_REMAINDER) build_rem_coeffs(p->m, p->h, p->c, p->tau, p->fwd32, &p->rem);
   if (is_tc_prec(p->prec)) {
     const int kind = p->prec == HERMITE_3XTF32 ? 0 : 1;
     p->tc_fwd = build_tc_btable(p->m, kind, p->fwd);
@@ -384,22 +391,22 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
   if (!(c > 0.0) || !std::isfinite(c)) return fail(HERMITE_EINVAL, "wave speed c must be positive");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(HERMITE_EINVAL, "time step dt must be positive");
   if (prec != HERMITE_FP64 && prec != HERMITE_FP32 && prec != HERMITE_HYBRID64 && prec != HERMITE_HYBRIDDF &&
-      !is_tc_prec(prec))
+      !is_tc_prec(prec) && prec != HERMITE_REMAINDER)
     return fail(HERMITE_EUNSUPPORTED, "precision %d not provided", prec);
   if (state_dtype != HERMITE_STATE_FP64 && state_dtype != HERMITE_STATE_FP32)
     return fail(HERMITE_EINVAL, "state type %d unknown", state_dtype);
   if (prec != HERMITE_FP32 && !is_tc_prec(prec) && state_dtype != HERMITE_STATE_FP64)
     return fail(HERMITE_EUNSUPPORTED, "FP64 and hybrid arithmetic need an FP64 state");
-  if (is_tc_prec(prec) && variant == HERMITE_SPLIT)
-    return fail(HERMITE_EUNSUPPORTED, "the tensor-core precisions run the fused kernel only");
+  if ((is_tc_prec(prec) || prec == HERMITE_REMAINDER) && variant == HERMITE_SPLIT)
+    return fail(HERMITE_EUNSUPPORTED, "the tensor-core and remainder-form precisions run the fused kernel only");
   if (variant != HERMITE_AUTO && variant != HERMITE_FUSED && variant != HERMITE_SPLIT)
     return fail(HERMITE_EINVAL, "variant %d unknown", variant);
   if (variant == HERMITE_SPLIT && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF))
     return fail(HERMITE_EUNSUPPORTED, "the split variant has no hybrid precision");
   if (q < 4 || q > 3 * (2 * m + 1))
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * m + 1), m);
-  if (q != 4 && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF || is_tc_prec(prec)))
-    return fail(HERMITE_EUNSUPPORTED, "the hybrid and tensor-core precisions run the 4-stage series only");
+  if (q != 4 && (prec == HERMITE_HYBRID64 || prec == HERMITE_HYBRIDDF || is_tc_prec(prec) || prec == HERMITE_REMAINDER))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid, tensor-core and remainder-form precisions run the 4-stage series only");
   const double tau = 0.5 * dt;
   if (int rc = check_stable(m, q, c, tau, h)) return rc;
   const size_t nodes = (size_t)grid[0] * grid[1] * grid[2];
@@ -509,8 +516,9 @@ int hermite_set_taylor_order(hermite_plan_t p, int q) {
   if (p->eq) return fail(HERMITE_EUNSUPPORTED, "advection plans fix q at hermite_adv_plan");
   if (q < 4 || q > 3 * (2 * p->m + 1))
     return fail(HERMITE_EINVAL, "q = %d outside 4..%d (3(2m+1)) for order %d", q, 3 * (2 * p->m + 1), p->m);
-  if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF || is_tc_prec(p->prec)))
-    return fail(HERMITE_EUNSUPPORTED, "the hybrid and tensor-core precisions run the 4-stage series only");
+  if (q != 4 && (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF || is_tc_prec(p->prec) ||
+                 p->prec == HERMITE_REMAINDER))
+    return fail(HERMITE_EUNSUPPORTED, "the hybrid, tensor-core and remainder-form precisions run the 4-stage series only");
   if (int rc = check_stable(p->m, q, p->c, p->tau, p->h)) return rc;
   p->q = q;
   p->evolve.q = q;
@@ -526,7 +534,7 @@ int hermite_schedule_count(hermite_plan_t p) {
   if (!p || p->batch) return 0;
   if (p->eq) return p->variant == HERMITE_SPLIT ? 1 : kAdvFusedTiles;
   if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
-  if (is_tc_prec(p->prec)) return 1;
+  if (is_tc_prec(p->prec) || p->prec == HERMITE_REMAINDER) return 1;
   return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
 }
 

@@ -150,6 +150,23 @@ cudaError_t launch_fused_tc(int kind, int m, int state, const void *in, void *ou
                             const StepCoeffs<float> &co, const TcBTable &bt, int zchunk, int *status,
                             cudaStream_t st);
 
+// Tables of the remainder-form kernel (remainder.cuh), per dimension d = x1,
+// x2, x3 and grade a of the 1-D factor G_a = lam^(2a)/a! T1 (d^2/dxi^2)^a H:
+// G_a [L; R] = ts_a L + rr_a rho with rho the remainder of the left node's
+// degree-m Taylor polynomial at the right node.
+struct RemCoeffs {
+  float ts[3][3][4][4];  // [d][a][r][j]: coefficient of xi^r of (d/dxi)^(2a) p_L (exact dyadic)
+  float rr[3][3][4][4];  // [d][a][r][i]: right-node block of T1 (d^2/dxi^2)^a H (exact dyadic)
+  float scale[3][3];     // [d][a]: lam_d^(2a)/a!
+  float beta[2][2][3];   // beta_c[fo][fi] of the 4-term series for the z-grades c of the grade-0 chain
+  float gy[3][16];       // right blocks of Gy_b (FP32), for Gy_b X_a with a >= 1
+  float kz[2][2][3][16]; // Kz[fo][fi][g] (FP32), for the y-results of grade g >= 1
+};
+void build_rem_coeffs(int m, const double h[3], double c, double tau, const StepCoeffs<float> &f32,
+                      RemCoeffs *out);
+cudaError_t launch_remainder(int m, const double *in, double *out, const Geom &g, const RemCoeffs &co, int zchunk,
+                             cudaStream_t st);
+
 // Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
 // output z-layers [z0, z0 + nzl); evolution reads it and writes the new node
 // data of those layers.

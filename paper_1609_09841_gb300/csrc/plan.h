@@ -30,6 +30,7 @@ struct hermite_plan_s {
   hermite::StepCoeffs<float> fwd32, adj32, dc32;
   hermite::HybridCoeffs hyb_fwd, hyb_adj, hyb_dc;
   hermite::TcBTable tc_fwd, tc_adj, tc_dc;  // tensor-core precisions: z-pass B operands
+  hermite::RemCoeffs rem;                   // remainder-form precision: forward tables
   int *status = nullptr;                    // device status word of the tensor-core kernel
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;

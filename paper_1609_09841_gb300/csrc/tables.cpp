@@ -203,4 +203,63 @@ void build_step_coeffs(int m, const double h[3], double c, double tau, int mode,
         }
 }
 
+// Remainder form of the 1-D factors (remainder.cuh).  With p_L(xi) =
+// sum_j L_j (xi + 1/2)^j the left node's Taylor polynomial of degree m, whose
+// data at the right node are sum_j C(j, i) L_j, linearity and the exactness of
+// Hermite interpolation on polynomials of degree <= 2m+1 give
+// G_a [L; R] = G_a [L; T L] + G_a [0; rho] = ts_a L + rr_a rho, where
+//   ts_a[r][j] = j!/(j-2a)! C(j-2a, r) 2^-(j-2a-r)   (coefficient of xi^r of
+//                (d/dxi)^(2a) p_L; zero unless j >= r + 2a)
+//   rr_a[r][i] = a!/lam^(2a) G_a[r][right node, i]
+// and scale_a = lam^(2a)/a!.  ts and rr are dyadic rationals, exact in float.
+void build_rem_coeffs(int m, const double h[3], double c, double tau, const StepCoeffs<float> &f32,
+                      RemCoeffs *out) {
+  const int M = m + 1, P = 2 * m + 2;
+  Q Hq[8][8];
+  exact_H(m, Hq);
+  *out = RemCoeffs{};
+  for (int d = 0; d < 3; ++d) {
+    const double lam2 = (c * tau / h[d]) * (c * tau / h[d]);
+    double scale = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      if (a > 0) scale *= lam2 / a;
+      for (int r = 0; r < M; ++r) {
+        for (int i = 0; i < M; ++i) {
+          double v = 0.0;
+          if (r + 2 * a < P) {
+            i128 fac = 1;
+            for (int qq = r + 1; qq <= r + 2 * a; ++qq) fac *= qq;
+            v = (Q(fac) * Hq[r + 2 * a][M + i]).to_double();
+          }
+          out->rr[d][a][r][i] = (float)v;
+        }
+        for (int j = 0; j < M; ++j) {
+          double v = 0.0;
+          if (j >= r + 2 * a) {
+            i128 fac = 1;
+            for (int qq = j - 2 * a + 1; qq <= j; ++qq) fac *= qq;   // j!/(j-2a)!
+            v = (Q(fac * binom(j - 2 * a, r), (i128)1 << (j - 2 * a - r))).to_double();
+          }
+          out->ts[d][a][r][j] = (float)v;
+        }
+      }
+      out->scale[d][a] = (float)scale;
+    }
+  }
+  // RK4 (the 4-term series): uu = vv = (1, 1/2, 1/12), uv = tau (1, 1/6, 0), vu = (0, 1, 1/3) / tau
+  const double b_uu[3] = {1.0, 0.5, 1.0 / 12}, b_uv[3] = {tau, tau / 6, 0.0}, b_vu[3] = {0.0, 1.0 / tau, 1.0 / (3 * tau)};
+  for (int k = 0; k < 3; ++k) {
+    out->beta[0][0][k] = (float)b_uu[k];
+    out->beta[1][1][k] = (float)b_uu[k];
+    out->beta[0][1][k] = (float)b_uv[k];
+    out->beta[1][0][k] = (float)b_vu[k];
+  }
+  for (int b = 0; b < 3; ++b)
+    for (int qq = 0; qq < 16; ++qq) out->gy[b][qq] = f32.gy[b][qq];
+  for (int fo = 0; fo < 2; ++fo)
+    for (int fi = 0; fi < 2; ++fi)
+      for (int g = 0; g < 3; ++g)
+        for (int qq = 0; qq < 16; ++qq) out->kz[fo][fi][g][qq] = f32.kz[fo][fi][g][qq];
+}
+
 }  // namespace hermite

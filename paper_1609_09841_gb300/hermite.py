@@ -12,7 +12,7 @@ from . import capi
 
 PRECISIONS = {"fp64": capi.HERMITE_FP64, "fp32": capi.HERMITE_FP32, "hybrid64": capi.HERMITE_HYBRID64,
               "hybriddf": capi.HERMITE_HYBRIDDF, "3xtf32": capi.HERMITE_3XTF32,
-              "splitbf16": capi.HERMITE_SPLITBF16}
+              "splitbf16": capi.HERMITE_SPLITBF16, "remainder": capi.HERMITE_REMAINDER}
 STATES = {"fp64": capi.HERMITE_STATE_FP64, "fp32": capi.HERMITE_STATE_FP32}
 VARIANTS = {"auto": capi.HERMITE_AUTO, "fused": capi.HERMITE_FUSED, "split": capi.HERMITE_SPLIT}
 
