@@ -176,6 +176,34 @@ int hermite_record(hermite_plan_t plan, const void *state, const long long *idx,
 int hermite_inject(hermite_plan_t plan, void *adj_state, const long long *idx, int count,
                    const double *w, void *stream);
 
+/* Testing hook for allocation failures: after this call, the next `skip`
+ * allocations of the library (host or device, in any plan or call) succeed
+ * and the `count` after them fail as if memory were exhausted, so that the
+ * calls that make them return HERMITE_ENOMEM and leave their plan usable.
+ * count = 0 disarms it.  Not thread-safe against concurrent allocations in
+ * other threads (the window is global).  EINVAL for negative arguments. */
+int hermite_inject_alloc_failure(long long skip, long long count);
+
+/* Debug build (the library compiled with -DHERMITE_DEBUG, libhermite_debug.so
+ * from the package's build script): every global load and store of a state
+ * in the fused kernels (FP64, FP32, hybrid, tensor-core and remainder-form
+ * precisions, single-grid plans) is checked against the state size; an
+ * out-of-range element offset is skipped (a load reads zero) and recorded.
+ * hermite_debug_build returns 1 for such a library, 0 otherwise.
+ * hermite_debug_status returns the flags raised since the last call (bit 1:
+ * a load, bit 2: a store out of range; 0 in release builds) and the smallest
+ * offending offset (~0 if none), then clears them; synchronises `stream`. */
+int hermite_debug_build(void);
+int hermite_debug_status(hermite_plan_t plan, int *flags, unsigned long long *first_index, void *stream);
+/* Self-test of the debug build's checks: one forward half step of device
+ * buffers in -> out (full-size states) in which the kernels are told that a
+ * state holds only fraction x hermite_state_elems(plan) elements; every access
+ * past that must be flagged and skipped (no access can leave the real
+ * buffers).  EUNSUPPORTED in release builds; EINVAL for fraction outside
+ * (0, 1], batched or advection plans and the buffer rules of hermite_step. */
+int hermite_debug_selftest(hermite_plan_t plan, const void *in, void *out, int parity, double fraction,
+                           void *stream);
+
 /* Device status of the plan's kernels: *status receives the OR of the flags
  * that kernels raised since the last call (0: none) and the flags are
  * cleared.  Bit 0: a CTA of the tensor-core kernel (HERMITE_3XTF32,

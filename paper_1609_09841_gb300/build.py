@@ -32,12 +32,12 @@ def _deps():
     return max(os.path.getmtime(h) for h in headers)
 
 
-def _compile(src, verbose):
+def _compile(src, verbose, objdir=OBJ, extra=()):
     path = os.path.join(CSRC, src)
-    obj = os.path.join(OBJ, src + ".o")
+    obj = os.path.join(objdir, src + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(path), _deps()):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + ["-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
     if src.endswith(".cpp"):
         cmd = [nvcc(), "-x", "cu"] + cmd[1:]
     if verbose:
@@ -50,22 +50,27 @@ def _compile(src, verbose):
     return obj
 
 
-def build(verbose=False, force=False):
-    """Compile and link; returns the path of libhermite.so."""
-    os.makedirs(OBJ, exist_ok=True)
+def build(verbose=False, force=False, debug=False):
+    """Compile and link; returns the path of libhermite.so, or with debug=True
+    of libhermite_debug.so (the same sources with -DHERMITE_DEBUG: bounds
+    checks in the fused kernels, objects in _build_debug)."""
+    objdir = OBJ + "_debug" if debug else OBJ
+    lib = os.path.join(HERE, "libhermite_debug.so") if debug else LIB
+    extra = ("-DHERMITE_DEBUG",) if debug else ()
+    os.makedirs(objdir, exist_ok=True)
     if force:
-        for f in os.listdir(OBJ):
-            os.remove(os.path.join(OBJ, f))
+        for f in os.listdir(objdir):
+            os.remove(os.path.join(objdir, f))
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+        objs = list(ex.map(lambda s: _compile(s, verbose, objdir, extra), SOURCES))
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath=/usr/local/cuda/lib64",
-                                  "-o", LIB] + objs + ["-lpthread"]
+                                  "-o", lib] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv, debug="--debug" in sys.argv))

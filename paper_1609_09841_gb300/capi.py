@@ -8,6 +8,7 @@ import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhermite.so")
+DEBUG_LIB_PATH = os.path.join(_HERE, "libhermite_debug.so")
 
 HERMITE_OK = 0
 HERMITE_EINVAL = -1
@@ -42,10 +43,13 @@ class HermiteError(RuntimeError):
         self.code = code
 
 
-def _load():
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"libhermite.so not built ({LIB_PATH}); run paper_1609_09841_gb300/build.py")
-    lib = ctypes.CDLL(LIB_PATH)
+def load_library(path=LIB_PATH):
+    """ctypes handle of a libhermite build (the release library by default;
+    the debug build is libhermite_debug.so beside it), with every signature
+    declared."""
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run paper_1609_09841_gb300/build.py")
+    lib = ctypes.CDLL(path)
     P, I, D, U, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint, ctypes.c_size_t
     IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
     sig = {
@@ -81,6 +85,10 @@ def _load():
         "hermite_set_schedule": (I, [P, I, I]),
         "hermite_dot": (I, [P, P, P, DP, P]),
         "hermite_device_status": (I, [P, IP, P]),
+        "hermite_inject_alloc_failure": (I, [ctypes.c_longlong, ctypes.c_longlong]),
+        "hermite_debug_build": (I, []),
+        "hermite_debug_status": (I, [P, IP, ctypes.POINTER(ctypes.c_ulonglong), P]),
+        "hermite_debug_selftest": (I, [P, P, P, I, D, P]),
         "hermite_record": (I, [P, P, P, I, P, P]),
         "hermite_inject": (I, [P, P, P, I, P, P]),
         "hermite_last_error": (ctypes.c_char_p, []),
@@ -92,7 +100,7 @@ def _load():
     return lib
 
 
-lib = _load()
+lib = load_library()
 
 
 def last_error():

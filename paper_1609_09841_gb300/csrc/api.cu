@@ -33,7 +33,34 @@ int fail(int code, const char *fmt, ...) {
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
-  return fail(HERMITE_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  const int code = e == cudaErrorMemoryAllocation ? HERMITE_ENOMEM : HERMITE_ECUDA;
+  return fail(code, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Injection window of the allocation gate: after g_alloc_skip more
+// allocations succeed, the next g_alloc_fail ones fail.
+std::atomic<long long> g_alloc_skip{0}, g_alloc_fail{0};
+
+bool alloc_injected_failure() {
+  if (g_alloc_fail.load(std::memory_order_relaxed) <= 0) return false;
+  if (g_alloc_skip.fetch_sub(1, std::memory_order_relaxed) > 0) return false;
+  return g_alloc_fail.fetch_sub(1, std::memory_order_relaxed) > 0;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  if (alloc_injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc_pinned(void **p, size_t bytes) {
+  if (alloc_injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
 }
 
 }  // namespace hermite
@@ -83,7 +110,24 @@ Geom geom_of(const hermite_plan_s *p, int s) {
   g.s = s;
   g.zlo = 0;
   g.zhi = g.nz;
+  g.elems = p->dbg_bound ? p->dbg_bound : p->elems;
+  g.dbg = p->dbg;
   return g;
+}
+
+// Debug build: the record of the kernels' bounds checks, allocated by the
+// first step of a plan (zero flags, no offending offset).
+int ensure_dbg(hermite_plan_s *p) {
+  if (!kDebugBuild || p->dbg) return HERMITE_OK;
+  cudaError_t e = dev_malloc((void **)&p->dbg, sizeof(DebugRecord));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->dbg = nullptr;
+    return fail(HERMITE_ENOMEM, "debug record");
+  }
+  const DebugRecord init{0, 0, ~0ull};
+  e = cudaMemcpy(p->dbg, &init, sizeof init, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "debug record");
 }
 
 int ensure_ws(hermite_plan_s *p, size_t bytes) {
@@ -91,7 +135,7 @@ int ensure_ws(hermite_plan_s *p, size_t bytes) {
   if (p->ws) cudaFree(p->ws);
   p->ws = nullptr;
   p->ws_bytes = 0;
-  cudaError_t e = cudaMalloc(&p->ws, bytes);
+  cudaError_t e = dev_malloc(&p->ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(HERMITE_ENOMEM, "split workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
@@ -105,14 +149,14 @@ int ensure_ws(hermite_plan_s *p, size_t bytes) {
 int ensure_red(hermite_plan_s *p) {
   if (p->red && p->red_host) return HERMITE_OK;
   if (!p->red) {
-    cudaError_t e = cudaMalloc(&p->red, sizeof(double) * (size_t)(error_blocks() + 1) * 8);
+    cudaError_t e = dev_malloc((void **)&p->red, sizeof(double) * (size_t)(error_blocks() + 1) * 8);
     if (e != cudaSuccess) {
       cudaGetLastError();
       p->red = nullptr;
       return fail(HERMITE_ENOMEM, "reduction scratch");
     }
   }
-  cudaError_t e = cudaMallocHost(&p->red_host, sizeof(double) * 8);
+  cudaError_t e = host_malloc_pinned((void **)&p->red_host, sizeof(double) * 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     p->red_host = nullptr;
@@ -176,6 +220,7 @@ int run_adv_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaS
 // mirrored corner offset).
 int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st, int zlo = 0,
              int zhi = -1) {
+  if (int rc = ensure_dbg(p)) return rc;
   if (p->eq == 1) return run_adv_step(p, in, out, parity, st, zlo, zhi);
   const int s_fwd = parity == 0 ? 0 : -1;
   const bool adjoint = mode == kAdjoint;
@@ -205,7 +250,7 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     }
     if (is_tc_prec(p->prec)) {
       if (!p->status) {
-        cudaError_t ea = cudaMalloc(&p->status, sizeof(int));
+        cudaError_t ea = dev_malloc((void **)&p->status, sizeof(int));
         if (ea != cudaSuccess) {
           cudaGetLastError();
           p->status = nullptr;
@@ -280,7 +325,7 @@ int host_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaStre
   if (overlaps(in, out, bytes)) return fail(HERMITE_EINVAL, "input and output states overlap");
   for (int k = 0; k < 2; ++k)
     if (!p->stage[k]) {
-      cudaError_t e = cudaMalloc(&p->stage[k], bytes);
+      cudaError_t e = dev_malloc(&p->stage[k], bytes);
       if (e != cudaSuccess) {
         cudaGetLastError();
         p->stage[k] = nullptr;
@@ -410,7 +455,7 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
   const double tau = 0.5 * dt;
   if (int rc = check_stable(m, q, c, tau, h)) return rc;
   const size_t nodes = (size_t)grid[0] * grid[1] * grid[2];
-  hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
+  hermite_plan_s *p = host_new<hermite_plan_s>();
   if (!p) return fail(HERMITE_ENOMEM, "plan allocation");
   p->m = m;
   for (int k = 0; k < 3; ++k) {
@@ -477,7 +522,7 @@ int hermite_adv_plan(hermite_plan_t *out, int m, const int grid[3], const double
       return fail(HERMITE_EUNSTABLE, "|a[%d]|*(dt/2)/h[%d] = %.6g above the stability limit %.3g of order %d, q = %d",
                   k, k, lam, adv_limit_of(m, q), m, q);
   }
-  hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
+  hermite_plan_s *p = host_new<hermite_plan_s>();
   if (!p) return fail(HERMITE_ENOMEM, "plan allocation");
   p->eq = 1;
   p->m = m;
@@ -641,6 +686,46 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
   return HERMITE_OK;
 }
 
+int hermite_inject_alloc_failure(long long skip, long long count) {
+  if (skip < 0 || count < 0) return fail(HERMITE_EINVAL, "negative skip or count");
+  g_alloc_fail.store(0, std::memory_order_relaxed);
+  g_alloc_skip.store(skip, std::memory_order_relaxed);
+  g_alloc_fail.store(count, std::memory_order_relaxed);
+  return HERMITE_OK;
+}
+
+int hermite_debug_build(void) { return kDebugBuild ? 1 : 0; }
+
+int hermite_debug_status(hermite_plan_t p, int *flags, unsigned long long *first, void *stream) {
+  if (!p || !flags || !first) return fail(HERMITE_EINVAL, "null argument");
+  *flags = 0;
+  *first = ~0ull;
+  if (!p->dbg) return HERMITE_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  DebugRecord r{};
+  const DebugRecord init{0, 0, ~0ull};
+  cudaError_t e = cudaMemcpyAsync(&r, p->dbg, sizeof r, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(p->dbg, &init, sizeof init, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "debug record read");
+  *flags = r.flags;
+  *first = r.first;
+  return HERMITE_OK;
+}
+
+int hermite_debug_selftest(hermite_plan_t p, const void *in, void *out, int parity, double fraction, void *stream) {
+  if (!kDebugBuild) return fail(HERMITE_EUNSUPPORTED, "not a debug build");
+  if (!p || p->batch || p->eq) return fail(HERMITE_EINVAL, "plan is NULL, batched or advection");
+  if (!(fraction > 0.0 && fraction <= 1.0)) return fail(HERMITE_EINVAL, "fraction %g outside (0, 1]", fraction);
+  if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
+  if (int rc = check_device_only(p, in, out, "hermite_debug_selftest")) return rc;
+  p->dbg_bound = (size_t)((double)p->elems * fraction);
+  if (p->dbg_bound == 0) p->dbg_bound = 1;
+  const int rc = run_step(p, in, out, parity, kForward, (cudaStream_t)stream);
+  p->dbg_bound = 0;
+  return rc;
+}
+
 int hermite_device_status(hermite_plan_t p, int *status, void *stream) {
   if (!p || !status) return fail(HERMITE_EINVAL, "null argument");
   *status = 0;
@@ -686,6 +771,7 @@ void hermite_destroy(hermite_plan_t p) {
   if (p->red) cudaFree(p->red);
   if (p->red_host) cudaFreeHost(p->red_host);
   if (p->status) cudaFree(p->status);
+  if (p->dbg) cudaFree(p->dbg);
   delete p;
 }
 

@@ -81,7 +81,7 @@ int build_items(BatchPlan *b) {
     }
   if (b->items) cudaFree(b->items);
   b->items = nullptr;
-  cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * items.size());
+  cudaError_t e = dev_malloc((void **)&b->items, sizeof(BatchItem) * items.size());
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(HERMITE_ENOMEM, "batched work list");
@@ -122,7 +122,7 @@ int get_set(BatchPlan *b, const void *const *in, void *const *out, BatchSim **de
   DescSet s;
   s.in.assign(in, in + b->nsims);
   s.out.assign(out, out + b->nsims);
-  cudaError_t e = cudaMalloc(&s.dev, sizeof(BatchSim) * b->nsims);
+  cudaError_t e = dev_malloc((void **)&s.dev, sizeof(BatchSim) * b->nsims);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(HERMITE_ENOMEM, "batch descriptors");
@@ -166,8 +166,8 @@ int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *
     if (rc) return rc;
     hermite_destroy(probe);
   }
-  hermite_plan_s *p = new (std::nothrow) hermite_plan_s();
-  BatchPlan *b = new (std::nothrow) BatchPlan();
+  hermite_plan_s *p = host_new<hermite_plan_s>();
+  BatchPlan *b = host_new<BatchPlan>();
   if (!p || !b) {
     delete p;
     delete b;
@@ -193,9 +193,9 @@ int hermite_batch_plan(hermite_plan_t *out, int nsims, const int *m, const int *
     build_step_coeffs(m[i], h + 3 * i, c[i], 0.5 * dt[i], kForward, 4, &cd);
     batch_write_record(b->compute, cd, host.data() + csize * i);
   }
-  cudaError_t e = cudaMalloc(&b->coeffs, host.size());
+  cudaError_t e = dev_malloc((void **)&b->coeffs, host.size());
   if (e == cudaSuccess) e = cudaMemcpy(b->coeffs, host.data(), host.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(int));
+  if (e == cudaSuccess) e = dev_malloc((void **)&b->counter, sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   int dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);

@@ -230,8 +230,8 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
       const TS *src = xsrc[k] + zoff;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        Lv[k][i] = (TC)__ldg(src + i * plane + xl[k]);
-        Rv[k][i] = (TC)__ldg(src + i * plane + xr[k]);
+        Lv[k][i] = (TC)state_load(g, in, src + i * plane + xl[k]);
+        Rv[k][i] = (TC)state_load(g, in, src + i * plane + xr[k]);
       }
     }
 #pragma unroll
@@ -431,7 +431,9 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
 #pragma unroll
         for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
-          for (int r = 0; r < M; ++r) o[(size_t)((fo * M + r) * M * M) * plane] = to_state<TS>(zacc[k][fo][r] + (E[fo][r] + O[fo][r]));
+          for (int r = 0; r < M; ++r)
+            state_store(g, out, &o[(size_t)((fo * M + r) * M * M) * plane],
+                        to_state<TS>(zacc[k][fo][r] + (E[fo][r] + O[fo][r])));
       }
 #pragma unroll
       for (int fo = 0; fo < 2; ++fo)

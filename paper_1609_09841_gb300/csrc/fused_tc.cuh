@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(NT, 2)
       const TS *src = xsrc[k] + zoff;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        Lv[k][i] = (TC)__ldg(src + i * plane + xl[k]);
-        Rv[k][i] = (TC)__ldg(src + i * plane + xr[k]);
+        Lv[k][i] = (TC)state_load(g, in, src + i * plane + xl[k]);
+        Rv[k][i] = (TC)state_load(g, in, src + i * plane + xr[k]);
       }
     }
 #pragma unroll
@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(NT, 2)
           for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
             for (int r = 0; r < M; ++r)
-              o[(size_t)((fo * M + r) * M * M) * plane] = state_from_float<TS>(zacc[fo][r] + v[fo * 4 + r]);
+              state_store(g, out, &o[(size_t)((fo * M + r) * M * M) * plane],
+                          state_from_float<TS>(zacc[fo][r] + v[fo * 4 + r]));
         }
 #pragma unroll
         for (int fo = 0; fo < 2; ++fo)

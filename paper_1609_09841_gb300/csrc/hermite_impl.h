@@ -6,11 +6,23 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <new>
 
 namespace hermite {
 
 constexpr int kMaxM = 4;  // largest M = m + 1
 constexpr int kMaxDevices = 64;  // device ordinals the per-device records below cover
+
+// Allocation gate: every host and device allocation of the library goes
+// through these, so that hermite_inject_alloc_failure (a testing hook) can
+// make chosen allocations fail as if memory were exhausted.
+bool alloc_injected_failure();  // consumes one allocation of the injection window
+cudaError_t dev_malloc(void **p, size_t bytes);          // cudaMalloc
+cudaError_t host_malloc_pinned(void **p, size_t bytes);  // cudaMallocHost
+template <typename T>
+T *host_new() {  // new (std::nothrow) T()
+  return alloc_injected_failure() ? nullptr : new (std::nothrow) T();
+}
 
 // Per-device record that a kernel's dynamic shared-memory limit has been
 // raised.  The attribute belongs to each device's context, so a launcher keeps
@@ -97,11 +109,68 @@ struct HybridCoeffs {
 };
 
 // Grid geometry of one launch.
+// Record of the debug build's bounds checks (device memory): the flags
+// raised (bit 1: a load, bit 2: a store outside the state) and the smallest
+// offending element offset.
+struct DebugRecord {
+  int flags;
+  int pad;
+  unsigned long long first;
+};
+
 struct Geom {
   int nx, ny, nz;
   int s;         // corner offset: corners of output node o are o + s + {0, 1} per dimension
   int zlo, zhi;  // output z layers [zlo, zhi) computed by a launch (the fused and hybrid kernels)
+  size_t elems = 0;             // elements of one state (debug build: the bound of every index; 0: unchecked)
+  DebugRecord *dbg = nullptr;   // debug build: where out-of-range accesses are recorded
 };
+
+// Bounds checks of the debug build (compiled with -DHERMITE_DEBUG): the
+// fused kernels route every global load and store of a state through these;
+// an element offset at or beyond g.elems raises `bit` and is recorded in
+// *g.dbg, and the access is skipped (a load returns zero).  Release builds
+// compile to the plain access.
+template <typename T>
+__device__ __forceinline__ T state_load(const Geom &g, const T *base, const T *ptr) {
+#ifdef HERMITE_DEBUG
+  const size_t off = (size_t)(ptr - base);
+  if (g.elems && off >= g.elems) {
+    if (g.dbg) {
+      atomicOr(&g.dbg->flags, 2);
+      atomicMin(&g.dbg->first, (unsigned long long)off);
+    }
+    return T(0);
+  }
+#else
+  (void)g;
+  (void)base;
+#endif
+  return __ldg(ptr);
+}
+template <typename T>
+__device__ __forceinline__ void state_store(const Geom &g, T *base, T *ptr, T v) {
+#ifdef HERMITE_DEBUG
+  const size_t off = (size_t)(ptr - base);
+  if (g.elems && off >= g.elems) {
+    if (g.dbg) {
+      atomicOr(&g.dbg->flags, 4);
+      atomicMin(&g.dbg->first, (unsigned long long)off);
+    }
+    return;
+  }
+#else
+  (void)g;
+  (void)base;
+#endif
+  *ptr = v;
+}
+constexpr bool kDebugBuild =
+#ifdef HERMITE_DEBUG
+    true;
+#else
+    false;
+#endif
 
 // Cells per CTA along x3 such that ceil(nzl / zchunk) CTAs fit gridDim.y
 // (and gridDim.z), at most 65535: the requested chunk, or a larger one.

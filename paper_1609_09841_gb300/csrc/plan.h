@@ -32,6 +32,8 @@ struct hermite_plan_s {
   hermite::TcBTable tc_fwd, tc_adj, tc_dc;  // tensor-core precisions: z-pass B operands
   hermite::RemCoeffs rem;                   // remainder-form precision: forward tables
   int *status = nullptr;                    // device status word of the tensor-core kernel
+  hermite::DebugRecord *dbg = nullptr;      // debug build: record of the kernels' bounds checks
+  size_t dbg_bound = 0;                     // debug self-test: bound handed to the kernels (0: elems)
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
   int q = 4;                // Taylor stages of the local evolution (4 = RK4)

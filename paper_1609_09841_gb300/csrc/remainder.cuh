@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(NT)
       const double *src = xsrc[k] + zoff;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        Lv[k][i] = __ldg(src + i * plane + xl[k]);
-        Rv[k][i] = __ldg(src + i * plane + xr[k]);
+        Lv[k][i] = state_load(g, in, src + i * plane + xl[k]);
+        Rv[k][i] = state_load(g, in, src + i * plane + xr[k]);
       }
     }
 #pragma unroll
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(NT)
                 for (int i = 0; i < M; ++i)
                   accf = fmaf(co.kz[fo][fi][gm + 1][r * 4 + i], (r & 1) ? d1[fi][gm][i] : s1[fi][gm][i], accf);
             }
-            o[(size_t)((fo * M + r) * M * M) * plane] = f2d_exact(acc.hi) + f2d_exact(acc.lo + accf);
+            state_store(g, out, &o[(size_t)((fo * M + r) * M * M) * plane], f2d_exact(acc.hi) + f2d_exact(acc.lo + accf));
           }
       }
     }
