@@ -15,7 +15,10 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhermite.so")
 SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu", "advect.cu", "symbol.cpp", "fused_tc.cu", "remainder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + \
+# -fno-gnu-unique: the function-local statics of template launchers (the per-device record that a
+# kernel's shared-memory limit was raised) stay private to each library, also when a process loads
+# the release and the debug build side by side (GNU-unique symbols would be shared between them).
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fno-gnu-unique", "--expt-relaxed-constexpr"] + \
     os.environ.get("HERMITE_NVCC_FLAGS", "").split()
 
 
