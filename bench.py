@@ -529,7 +529,7 @@ def run_advection(torch, rank, world, max_over_ranks, hbm_peak, side=150, nsteps
                 for k in range(2 * nsteps):
                     p64.step(a64, b64, k % 2)
                     a64, b64 = b64, a64
-                (max_abs, max_rel, rms, l2_rel), _ = plan.error(a, a64, mask=0b101)
+                (max_abs, max_rel, l2_abs, l2_rel), _ = plan.error(a, a64, mask=0b101)
                 row["fp32_vs_fp64_end_state"] = {"max_rel_all_components": max_rel, "l2_rel": l2_rel}
                 del p64, a64, b64
             del plan

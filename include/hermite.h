@@ -147,7 +147,7 @@ int hermite_adjoint_step(hermite_plan_t plan, const void *out_adj, void *in_adj,
  * same layout), both device pointers, over the components selected by
  * component_mask: bit0 field u, bit1 field v, bit2 all derivative orders
  * (else the values i = (0,0,0) only).  out[0] = max|a-b|, out[1] =
- * max|a-b| / max|b|, out[2] = sqrt(mean (a-b)^2), out[3] = ||a-b||_2/||b||_2.
+ * max|a-b| / max|b|, out[2] = ||a-b||_2, out[3] = ||a-b||_2/||b||_2.
  * FP64 reduction on the device; synchronises `stream`.  Returns ENONFINITE
  * (with out filled) if any selected entry of either array is NaN or Inf. */
 int hermite_error(hermite_plan_t plan, const void *state, const void *ref, unsigned component_mask,

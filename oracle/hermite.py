@@ -407,8 +407,8 @@ def adjoint_half_step_literal(G, m, h, c, dt, parity):
 def error_norms(a, b, component_mask=0b111):
     """(max_abs, max_rel, l2_abs, l2_rel) of a - b over the selected
     components: bit0 field u, bit1 field v, bit2 all derivative orders (else
-    the values i = (0,0,0) only).  max_rel = max|a-b| / max|b|, l2_abs = the
-    root mean square of a - b, l2_rel = ||a-b||_2 / ||b||_2."""
+    the values i = (0,0,0) only).  max_rel = max|a-b| / max|b|, l2_abs =
+    ||a-b||_2, l2_rel = ||a-b||_2 / ||b||_2."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     fields = [f for f in (0, 1) if component_mask >> f & 1]
@@ -422,7 +422,7 @@ def error_norms(a, b, component_mask=0b111):
     l2 = float(np.sum(d * d))
     l2b = float(np.sum(sb * sb))
     return (max_abs, max_abs / max_b if max_b > 0 else np.inf,
-            float(np.sqrt(l2 / max(d.size, 1))), float(np.sqrt(l2 / l2b)) if l2b > 0 else np.inf)
+            float(np.sqrt(l2)), float(np.sqrt(l2 / l2b)) if l2b > 0 else np.inf)
 
 
 def energy(S, m, h, c, parity_of_grid=0):

@@ -676,11 +676,9 @@ int hermite_error(hermite_plan_t p, const void *state, const void *ref, unsigned
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
   const double *r = p->red_host;
-  const int nc = (p->m + 1) * (p->m + 1) * (p->m + 1);
-  const double count = (double)plane * (((mask & 1u) ? 1 : 0) + ((mask & 2u) ? 1 : 0)) * ((mask & 4u) ? nc : 1);
   out[0] = r[0];
   out[1] = r[1] > 0 ? r[0] / r[1] : INFINITY;
-  out[2] = std::sqrt(r[2] / count);
+  out[2] = std::sqrt(r[2]);
   out[3] = r[3] > 0 ? std::sqrt(r[2] / r[3]) : INFINITY;
   if (r[4] > 0) return fail(HERMITE_ENONFINITE, "%.0f non-finite entries", r[4]);
   return HERMITE_OK;

@@ -185,7 +185,7 @@ class Plan:
         return adj
 
     def error(self, x, ref, mask=0b111, stream=None):
-        """(max_abs, max_rel, rms, l2_rel) of x - ref (ref FP64, device tensors)."""
+        """(max_abs, max_rel, l2_abs, l2_rel) of x - ref (ref FP64, device tensors)."""
         self._check(x)
         if tuple(ref.shape) != self.shape or not _is_fp64(ref):
             raise ValueError(f"ref must be a float64 state of shape {self.shape}")
@@ -237,7 +237,7 @@ class AdvectionPlan(Plan):
         return (M, M, M, self.grid[2], self.grid[1], self.grid[0])
 
     def error(self, x, ref, mask=0b101, stream=None):
-        """(max_abs, max_rel, rms, l2_rel) of x - ref (one field; mask bit 4:
+        """(max_abs, max_rel, l2_abs, l2_rel) of x - ref (one field; mask bit 4:
         every derivative component, else values only)."""
         return super().error(x, ref, mask, stream)
 
