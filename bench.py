@@ -439,7 +439,7 @@ def run_ours(args, rank, world):
     kern = {"fp32": "fused_step_kernel<float, float, ...>", "fp32_s64": "fused_step_kernel<double, float, ...>",
             "3xtf32": "tc_step_kernel<..., 3xTF32>", "splitbf16": "tc_step_kernel<..., BF16x3>",
             "hybriddf": "hybrid_step_kernel<HiDF, ...>", "hybrid64": "hybrid_step_kernel<HiF64, ...>",
-            "remainder": "rem_step_kernel<4, 8, 4, 512>",
+            "remainder": "rem_step_kernel (m = 3: tile 0 <4, 8, 4, 512>, tile 1 <4, 8, 2, 256, 2>, tile 2 <4, 4, 4, 256, 2>)",
             "fp64": "fused_step_kernel<double, double, ...>"}
     cfg = bench_config(world, m, args.side)
     out = {
@@ -456,7 +456,7 @@ def run_ours(args, rank, world):
                      "bytes_per_launch": hr["bytes_per_step"],
                      "bytes_rule": f"one state read + one written: 2 x 2(m+1)^3 x {8 if state == 'fp64' else 4} B "
                                    f"per node x {args.side}^3 nodes",
-                     "kernel": kern.get(head),
+                     "kernel": kern.get(head), "schedule": hr["schedule"],
                      "alu_nominal": {"flop_per_node": FLOP_PER_NODE[m],
                                      "tflops": FLOP_PER_NODE[m] * args.side ** 3 / (hr["ms_per_step"] * 1e-3) / 1e12,
                                      "note": "nominal: the kernel's factorised flop count, no measured peak"}},

@@ -244,7 +244,7 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     const StepCoeffs<float> &cf = mode == kAdjoint ? p->adj32 : (mode == kDc ? p->dc32 : p->fwd32);
     if (p->prec == HERMITE_REMAINDER) {
       if (mode != kForward) return fail(HERMITE_EUNSUPPORTED, "the remainder-form precision has forward steps only");
-      e = launch_remainder(p->m, (const double *)in, (double *)out, g, p->rem, p->zchunk, st);
+      e = launch_remainder(p->m, p->tile, (const double *)in, (double *)out, g, p->rem, p->zchunk, st);
       if (e != cudaSuccess) return cuda_fail(e, "remainder-form half-step launch");
       return HERMITE_OK;
     }
@@ -476,7 +476,7 @@ int hermite_plan_taylor(hermite_plan_t *out, int m, const int grid[3], const dou
   for (int k = 0; k < 3; ++k) p->evolve.c2h[k] = c * c / (h[k] * h[k]);
   p->evolve.q = q;
   build_interp_coeffs(m, &p->interp);
-  p->tile = 0;
+  p->tile = prec == HERMITE_REMAINDER ? 1 : 0;  // remainder form: two CTAs per SM (measured at m = 3, 256^3)
   p->zchunk = 16;
   p->ws_limit = (size_t)1 << 30;
   *out = p;
@@ -579,7 +579,8 @@ int hermite_schedule_count(hermite_plan_t p) {
   if (!p || p->batch) return 0;
   if (p->eq) return p->variant == HERMITE_SPLIT ? 1 : kAdvFusedTiles;
   if (p->prec == HERMITE_HYBRID64 || p->prec == HERMITE_HYBRIDDF) return hybrid_tile_count();
-  if (is_tc_prec(p->prec) || p->prec == HERMITE_REMAINDER) return 1;
+  if (p->prec == HERMITE_REMAINDER) return remainder_tile_count();
+  if (is_tc_prec(p->prec)) return 1;
   return fused_tile_count(p->prec == HERMITE_FP64 ? 0 : 1, p->m);
 }
 

@@ -233,8 +233,9 @@ struct RemCoeffs {
 };
 void build_rem_coeffs(int m, const double h[3], double c, double tau, const StepCoeffs<float> &f32,
                       RemCoeffs *out);
-cudaError_t launch_remainder(int m, const double *in, double *out, const Geom &g, const RemCoeffs &co, int zchunk,
-                             cudaStream_t st);
+int remainder_tile_count();
+cudaError_t launch_remainder(int m, int tile, const double *in, double *out, const Geom &g, const RemCoeffs &co,
+                             int zchunk, cudaStream_t st);
 
 // Split pair.  Interpolation writes Ru[f][jz][jy][jx][cell] for the cells of
 // output z-layers [z0, z0 + nzl); evolution reads it and writes the new node

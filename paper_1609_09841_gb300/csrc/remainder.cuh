@@ -19,9 +19,9 @@
 //
 // The remainders and the grade-0 chain (the x-interpolant X_0 of the node
 // data, the y-interpolant Y_0 of X_0, the z-interpolant of Y_0 that is the
-// main part of the output) need more than FP32.  Their coefficients are short
-// dyadic numbers (C(j,i) <= 3, 2^-k, and RR_0 with 11-bit numerators), so they
-// are evaluated as exact sums: each input x of an item is split on a
+// main part of the output) need more than FP32.  The remainder and the Taylor
+// shift to the centre have short dyadic coefficients (C(j,i) <= 3, 2^-k), so
+// they are evaluated as exact sums (RR_0 rho, small, is added in FP32): each input x of an item is split on a
 // power-of-two grid q fixed per item (x = h + l, h an integer multiple of q,
 // |h| <= 2^B q, |l| <= q/2); every product c h is then a multiple of q times
 // the coefficient's denominator, and every partial sum stays below 2^24 such
@@ -45,12 +45,10 @@
 
 namespace hermite {
 
-// Grid bits of the exact sums: B_IN for sums over node data, X_0 or Y_0
-// (Taylor shift TS_0 with entries C(j,r) 2^-(j-r), row sums <= 27/8 over the
-// denominator 8; remainder with row sums <= 7: 27 * 2^18 < 2^24), B_RHO for
-// RR_0 applied to the remainder (entries over 2^7, row sums <= 14.6 at m = 3:
-// 14.6 * 2^7 * 2^12 < 2^23).
-constexpr int kRemBitsIn = 18, kRemBitsRho = 12;
+// Grid bits of the exact sums over node data, X_0 or Y_0 (Taylor shift TS_0
+// with entries C(j,r) 2^-(j-r), row sums <= 27/8 over the denominator 8;
+// remainder with row sums <= 7: 27 * 2^18 < 2^24).
+constexpr int kRemBitsIn = 18;
 
 __host__ __device__ constexpr int binom_c(int n, int k) {
   int r = 1;
@@ -105,39 +103,31 @@ __device__ __forceinline__ void rem_edge(const unsigned long long (&Lp)[M], cons
   }
 }
 
-// x0 += RR_0 rho, and rho collapsed to floats for the FP32 parts.  RR_0 rho
-// is summed exactly on rho's own grid (much finer than x0's), then merged with
-// x0 by an error-free TwoSum of the leading parts: x0 becomes a normalised
-// pair (s, e + l0 + l1) accurate to about 2^-47 of |x0|.
+// x0 += RR_0 rho, and rho collapsed to floats for the FP32 parts.  rho is
+// about (kh)^(m+1)/(m+1)! of the field, so RR_0 rho in FP32 (row sums <= 14.6)
+// is off by about 2^-24 x 14.6 |rho|, 2^-39 of the field at kh = 0.08; it is
+// merged with the exact Taylor shift by an error-free TwoSum of the leading
+// parts, and x0 becomes a normalised pair.  (An exact sum of RR_0 rho on rho's
+// own grid measured 3.9e-7 at t = 1 on the 128^3 precision workload against
+// 4.7e-7 this way, at 8 % more time.)
 template <int M>
 __device__ __forceinline__ void rem_add_rr0(const float (&rr0)[4][4], const unsigned long long (&rho)[M],
                                             unsigned long long (&x0)[M], float (&rf)[M]) {
-  float mx = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     float h, l;
     unpack2f(rho[i], h, l);
     rf[i] = h + l;
-    mx = fmaxf(mx, fabsf(h));
-  }
-  const float C = grid_constant<kRemBitsRho>(mx);
-  unsigned long long rp[M];
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    float h, l;
-    unpack2f(rho[i], h, l);
-    rp[i] = grid_split(h, l, C);
   }
 #pragma unroll
   for (int r = 0; r < M; ++r) {
-    unsigned long long acc = 0ull;
+    float t = 0.f;
 #pragma unroll
-    for (int i = 0; i < M; ++i) acc = fma2f(pack2f(rr0[r][i], rr0[r][i]), rp[i], acc);
-    float h0, l0, h1, l1;
+    for (int i = 0; i < M; ++i) t = fmaf(rr0[r][i], rf[i], t);
+    float h0, l0;
     unpack2f(x0[r], h0, l0);
-    unpack2f(acc, h1, l1);
-    const df32 t = df_two_sum(h0, h1);
-    x0[r] = pack2f(t.hi, t.lo + (l0 + l1));
+    const df32 q = df_two_sum(h0, t);
+    x0[r] = pack2f(q.hi, q.lo + l0);
   }
 }
 
@@ -180,8 +170,8 @@ __device__ __forceinline__ void rem_grades(const float (&ts)[3][4][4], const flo
   }
 }
 
-template <int M, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT)
+template <int M, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     rem_step_kernel(const double *__restrict__ in, double *__restrict__ out, const Geom g, int zchunk,
                     const RemCoeffs co) {
   using H = df32;  // (h, l) pairs in shared memory
@@ -459,11 +449,11 @@ __global__ void __launch_bounds__(NT)
   }
 }
 
-template <int M, int TX, int TY, int NT>
+template <int M, int TX, int TY, int NT, int MINB = 1>
 cudaError_t launch_rem_cfg(const double *in, double *out, const Geom &g, const RemCoeffs &co, int zchunk,
                            cudaStream_t st) {
   using Sh = HybridShape<M, TX, TY>;
-  auto kern = rem_step_kernel<M, TX, TY, NT>;
+  auto kern = rem_step_kernel<M, TX, TY, NT, MINB>;
   static SmemAttrOnce smem_once;  // per instantiation, per device
   if (cudaError_t e = raise_smem_limit(smem_once, kern, Sh::SMEM); e != cudaSuccess) return e;
   if (zchunk <= 0) zchunk = 16;

@@ -31,4 +31,4 @@ def test_remainder_plan_rules():
             Plan(2, n, h, 1.0, 0.4 / 8, prec="remainder", **kw)
         assert e.value.code == code, kw
     p = Plan(3, n, h, 1.0, 0.4 / 8, prec="remainder")
-    assert p.schedule_count() == 1
+    assert p.schedule_count() == 3
