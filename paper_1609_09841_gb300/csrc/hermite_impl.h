@@ -230,6 +230,9 @@ struct RemCoeffs {
   float beta[2][2][3];   // beta_c[fo][fi] of the 4-term series for the z-grades c of the grade-0 chain
   float gy[3][16];       // right blocks of Gy_b (FP32), for Gy_b X_a with a >= 1
   float kz[2][2][3][16]; // Kz[fo][fi][g] (FP32), for the y-results of grade g >= 1
+  // the same as pairs of rows (r, r+1) = (2 rp, 2 rp + 1) for fma.rn.f32x2 (low word row 2 rp)
+  unsigned long long gy2[3][2][4];        // [b][rp][i]
+  unsigned long long kz2[2][2][2][2][4];  // [fo][fi][g - 1][rp][i]
 };
 void build_rem_coeffs(int m, const double h[3], double c, double tau, const StepCoeffs<float> &f32,
                       RemCoeffs *out);

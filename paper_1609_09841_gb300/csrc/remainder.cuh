@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(NT, MINB)
       if (yd0[k] < 0) continue;
       H L0[M], R0[M];
       float sa[NA - 1][M], da[NA - 1][M];
+      unsigned long long sda[NA - 1][M];  // (sum, difference) butterfly pairs of X_a, a >= 1
       float mx = 0.f;
 #pragma unroll
       for (int iy = 0; iy < M; ++iy) {
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(NT, MINB)
           const float Lf = xf[0], Rf = xf[TX];
           sa[a - 1][iy] = (iy & 1) ? Rf - Lf : Rf + Lf;
           da[a - 1][iy] = (iy & 1) ? Rf + Lf : Rf - Lf;
+          sda[a - 1][iy] = pack2f(sa[a - 1][iy], da[a - 1][iy]);
         }
       }
       const float C = grid_constant<kRemBitsIn>(mx);
@@ -339,19 +341,36 @@ __global__ void __launch_bounds__(NT, MINB)
         y0o[r * M * YS] = df32{h, l};
       }
 #pragma unroll
-      for (int gg = 1; gg < 3; ++gg)
+      for (int gg = 1; gg < 3; ++gg) {
+        // rows (2 rp, 2 rp + 1) share their inputs: (sum, difference) pairs
 #pragma unroll
-        for (int r = 0; r < M; ++r) {
+        for (int rp = 0; rp < M / 2; ++rp) {
+          unsigned long long acc2 = gg < NA ? pack2f(yg[gg - 1][2 * rp], yg[gg - 1][2 * rp + 1]) : 0ull;
+#pragma unroll
+          for (int a = 1; a < NA; ++a) {
+            const int b = gg - a;
+            if (b < 0 || b >= NA) continue;
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc2 = fma2f(co.gy2[b][rp][i], sda[a - 1][i], acc2);
+          }
+          float lo, hi;
+          unpack2f(acc2, lo, hi);
+          y1o[((gg - 1) * M * M * M + 2 * rp * M) * YS] = lo;
+          y1o[((gg - 1) * M * M * M + (2 * rp + 1) * M) * YS] = hi;
+        }
+        if constexpr (M & 1) {
+          constexpr int r = M - 1;
           float accf = gg < NA ? yg[gg - 1][r] : 0.f;
 #pragma unroll
           for (int a = 1; a < NA; ++a) {
             const int b = gg - a;
             if (b < 0 || b >= NA) continue;
 #pragma unroll
-            for (int i = 0; i < M; ++i) accf = fmaf(co.gy[b][r * 4 + i], (r & 1) ? da[a - 1][i] : sa[a - 1][i], accf);
+            for (int i = 0; i < M; ++i) accf = fmaf(co.gy[b][r * 4 + i], sa[a - 1][i], accf);
           }
           y1o[((gg - 1) * M * M * M + r * M) * YS] = accf;
         }
+      }
     }
     __syncthreads();
     // ---- z-pass: remainder form on Y_0 (the output's main part exact), FP32 for Y_1, Y_2 ----
@@ -396,7 +415,8 @@ __global__ void __launch_bounds__(NT, MINB)
             for (int c = 1; c < 3; ++c) zf[fi][c][r] = c < NA ? zg[c - 1][r] : 0.f;
           }
         }
-        float s1[2][2][M], d1[2][2][M];
+        float s1[2][2][M];
+        unsigned long long sd1[2][2][M];  // (sum, difference) butterfly pairs of Y_1, Y_2
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
@@ -406,9 +426,36 @@ __global__ void __launch_bounds__(NT, MINB)
               const int q1 = zs[k] + ((f * 2 + gm) * M + iz) * M * M * YS;
               const float Lf = p1[q1], Rf = c1[q1];
               s1[f][gm][iz] = (iz & 1) ? Rf - Lf : Rf + Lf;
-              d1[f][gm][iz] = (iz & 1) ? Rf + Lf : Rf - Lf;
+              sd1[f][gm][iz] = pack2f(s1[f][gm][iz], (iz & 1) ? Rf + Lf : Rf - Lf);
             }
         double *o = out + (size_t)(z0 + p - 1) * pxy + zxy[k] + (size_t)zcomp[k] * plane;
+        // Kz[g >= 1] on the y-results of grade >= 1, rows (2 rp, 2 rp + 1) in one fma.rn.f32x2
+        float yres[2][M];
+#pragma unroll
+        for (int fo = 0; fo < 2; ++fo) {
+#pragma unroll
+          for (int rp = 0; rp < M / 2; ++rp) {
+            unsigned long long acc2 = 0ull;
+#pragma unroll
+            for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+              for (int gm = 0; gm < 2; ++gm)
+#pragma unroll
+                for (int i = 0; i < M; ++i) acc2 = fma2f(co.kz2[fo][fi][gm][rp][i], sd1[fi][gm][i], acc2);
+            unpack2f(acc2, yres[fo][2 * rp], yres[fo][2 * rp + 1]);
+          }
+          if constexpr (M & 1) {
+            constexpr int r = M - 1;
+            float t = 0.f;
+#pragma unroll
+            for (int fi = 0; fi < 2; ++fi)
+#pragma unroll
+              for (int gm = 0; gm < 2; ++gm)
+#pragma unroll
+                for (int i = 0; i < M; ++i) t = fmaf(co.kz[fo][fi][gm + 1][r * 4 + i], s1[fi][gm][i], t);
+            yres[fo][r] = t;
+          }
+        }
 #pragma unroll
         for (int fo = 0; fo < 2; ++fo)
 #pragma unroll
@@ -430,18 +477,11 @@ __global__ void __launch_bounds__(NT, MINB)
               const df32 t = df_two_sum(acc.hi, p);
               acc = df_fast_two_sum(t.hi, t.lo + (acc.lo + fmaf(bx, lx, e)));
             }
-            float accf = 0.f;
+            float accf = yres[fo][r];
 #pragma unroll
-            for (int fi = 0; fi < 2; ++fi) {
+            for (int fi = 0; fi < 2; ++fi)
 #pragma unroll
-              for (int c = 0; c < 3; ++c)
-                if (c > 0) accf = fmaf(co.beta[fo][fi][c], zf[fi][c][r], accf);
-#pragma unroll
-              for (int gm = 0; gm < 2; ++gm)
-#pragma unroll
-                for (int i = 0; i < M; ++i)
-                  accf = fmaf(co.kz[fo][fi][gm + 1][r * 4 + i], (r & 1) ? d1[fi][gm][i] : s1[fi][gm][i], accf);
-            }
+              for (int c = 1; c < 3; ++c) accf = fmaf(co.beta[fo][fi][c], zf[fi][c][r], accf);
             state_store(g, out, &o[(size_t)((fo * M + r) * M * M) * plane], f2d_exact(acc.hi) + f2d_exact(acc.lo + accf));
           }
       }

@@ -9,6 +9,7 @@
 // elimination on fractions of 128-bit integers and rounded to double once.
 #include <cstdint>
 #include <cstdlib>
+#include <cstring>
 
 #include "hermite_impl.h"
 
@@ -260,6 +261,21 @@ void build_rem_coeffs(int m, const double h[3], double c, double tau, const Step
     for (int fi = 0; fi < 2; ++fi)
       for (int g = 0; g < 3; ++g)
         for (int qq = 0; qq < 16; ++qq) out->kz[fo][fi][g][qq] = f32.kz[fo][fi][g][qq];
+  auto pair = [](float lo, float hi) {
+    unsigned a, b;
+    std::memcpy(&a, &lo, 4);
+    std::memcpy(&b, &hi, 4);
+    return ((unsigned long long)b << 32) | a;
+  };
+  for (int rp = 0; rp < 2; ++rp)
+    for (int i = 0; i < 4; ++i) {
+      for (int b = 0; b < 3; ++b) out->gy2[b][rp][i] = pair(out->gy[b][2 * rp * 4 + i], out->gy[b][(2 * rp + 1) * 4 + i]);
+      for (int fo = 0; fo < 2; ++fo)
+        for (int fi = 0; fi < 2; ++fi)
+          for (int g = 1; g < 3; ++g)
+            out->kz2[fo][fi][g - 1][rp][i] =
+                pair(out->kz[fo][fi][g][2 * rp * 4 + i], out->kz[fo][fi][g][(2 * rp + 1) * 4 + i]);
+    }
 }
 
 }  // namespace hermite
