@@ -240,6 +240,16 @@ size_t hermite_batch_elems(hermite_plan_t plan, int sim);
  * work list and drops cached descriptor sets and graphs.  Default 16. */
 int hermite_batch_set_schedule(hermite_plan_t plan, const int zchunk[3]);
 
+/* Tile shape index (0 or 1, see hermite_batch_tile_shape) for orders 1, 2,
+ * 3; rebuilds the work list and drops cached descriptor sets and graphs.
+ * Default 0 for every order.  Results do not depend on the shape. */
+int hermite_batch_set_tiles(hermite_plan_t plan, const int tile[3]);
+
+/* The xy-tile (tx cells along x1, ty along x2) of tile shape `tile` of
+ * order m in the batched kernel: m = 1: 16x8, 8x8; m = 2: 16x4, 8x4;
+ * m = 3: 8x2, 4x4.  EINVAL outside m in 1..3, tile in 0..1. */
+int hermite_batch_tile_shape(int m, int tile, int *tx, int *ty);
+
 /* One half step of every simulation: out[i] = S_parity(in[i]).  in and out
  * are arrays of nsims device pointers.  The first call with a given pointer
  * set uploads a descriptor array (synchronously) and keeps it for later calls. */

@@ -1,11 +1,16 @@
-"""Autotuner of the fused kernel's schedule (tile shape x z-chunk).
+"""Autotuner of the kernels' schedules (tile shape x z-chunk).
 
-For a plan and a pair of device states it times every compiled tile shape
-(hermite_schedule_count) with each candidate z-chunk on the device (CUDA
-events, after a warm-up launch), keeps the fastest, applies it to the plan
-and caches it in a JSON file keyed by GPU name, order, precision, state type
-and grid.  The tuning launches are real half steps of the caller's states
-(their contents are overwritten).
+``tune``: for a single plan and a pair of device states it times every
+compiled tile shape (hermite_schedule_count) with each candidate z-chunk on
+the device (CUDA events, after a warm-up launch), keeps the fastest, applies
+it to the plan and caches it in a JSON file keyed by GPU name, order,
+precision, state type and grid.
+
+``tune_batch``: for a batched plan it picks a tile shape and a z-chunk per
+order (the per-m schedules of the one persistent launch).
+
+The tuning launches are real half steps of the caller's states (their
+contents are overwritten).
 """
 import json
 import os
@@ -66,29 +71,57 @@ def tune(plan, x, y, zchunks=ZCHUNKS, reps=2, cache=DEFAULT_CACHE, force=False):
     return best
 
 
-BATCH_ZCHUNKS = ((8, 8, 8), (16, 16, 16), (32, 16, 8), (32, 32, 16), (64, 32, 16), (96, 48, 32))
+BATCH_ZCHUNKS = (8, 16, 32, 64)
+BATCH_TILES = (0, 1)
 
 
-def tune_batch(bplan, a, b, options=BATCH_ZCHUNKS, reps=2):
-    """Pick and apply the fastest per-order z-chunks of a batched plan by
-    timing `reps` batched half steps for each option; returns
-    {"zchunk", "ms", "table"}."""
+def _time_batch(bplan, a, b, reps):
     import torch
+    bplan.step(a, b, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(reps):
+        if r % 2 == 0:
+            bplan.step(a, b, 0)
+        else:
+            bplan.step(b, a, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, reps=3, sweeps=2):
+    """Pick and apply the fastest tile shape x z-chunk of every order present
+    in a batched plan.  The orders share one persistent launch, so they are
+    tuned by coordinate search: for each order in turn (heaviest first) every
+    (tile, zchunk) pair is timed with the other orders held at their current
+    choice, and the fastest is kept; `sweeps` passes over the orders.  Timing:
+    `reps` batched half steps after a warm-up one (CUDA events).  Returns
+    {"tile", "zchunk" (per order 1..3), "ms", "table" (every timing)}."""
+    orders = sorted({s["m"] for s in bplan.sims}, reverse=True)
+    tile, zc = [0, 0, 0], [16, 16, 16]
+    bplan.set_tiles(tile)
+    bplan.set_schedule(zc)
     table = {}
-    for zc in options:
-        bplan.set_schedule(zc)
-        bplan.step(a, b, 0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for r in range(reps):
-            if r % 2 == 0:
-                bplan.step(a, b, 0)
-            else:
-                bplan.step(b, a, 1)
-        e1.record()
-        torch.cuda.synchronize()
-        table[zc] = e0.elapsed_time(e1) / reps
-    best = min(table, key=table.get)
-    bplan.set_schedule(best)
-    return {"zchunk": list(best), "ms": table[best], "table": {str(k): v for k, v in table.items()}}
+    best_ms = _time_batch(bplan, a, b, reps)
+    table[f"start {tile} {zc}"] = best_ms
+    for sweep in range(sweeps):
+        for m in orders:
+            choice = (tile[m - 1], zc[m - 1])
+            for t in tiles:
+                for z in zchunks:
+                    if (t, z) == choice:
+                        continue
+                    tt, zz = list(tile), list(zc)
+                    tt[m - 1], zz[m - 1] = t, z
+                    bplan.set_tiles(tt)
+                    bplan.set_schedule(zz)
+                    ms = _time_batch(bplan, a, b, reps)
+                    table[f"sweep {sweep} m={m} tile={t} zchunk={z}"] = ms
+                    if ms < best_ms:
+                        best_ms, choice = ms, (t, z)
+            tile[m - 1], zc[m - 1] = choice
+    bplan.set_tiles(tile)
+    bplan.set_schedule(zc)
+    return {"tile": tile, "zchunk": zc, "ms": best_ms, "table": table}

@@ -69,6 +69,17 @@ class BatchPlan:
     def set_schedule(self, zchunk):
         capi.check(capi.lib.hermite_batch_set_schedule(self.handle, (ctypes.c_int * 3)(*[int(v) for v in zchunk])))
 
+    def set_tiles(self, tile):
+        """Tile shape index (0 or 1) per order 1, 2, 3."""
+        capi.check(capi.lib.hermite_batch_set_tiles(self.handle, (ctypes.c_int * 3)(*[int(v) for v in tile])))
+
+    @staticmethod
+    def tile_shape(m, tile):
+        """(tx, ty) of the batched kernel's tile shape `tile` of order m."""
+        tx, ty = ctypes.c_int(), ctypes.c_int()
+        capi.check(capi.lib.hermite_batch_tile_shape(int(m), int(tile), ctypes.byref(tx), ctypes.byref(ty)))
+        return tx.value, ty.value
+
     def close(self):
         if self._h is not None:
             capi.lib.hermite_destroy(self._h)

@@ -80,6 +80,8 @@ def load_library(path=LIB_PATH):
         "hermite_batch_plan": (I, [ctypes.POINTER(P), I, IP, IP, DP, DP, DP, I, I]),
         "hermite_batch_elems": (S, [P, I]),
         "hermite_batch_set_schedule": (I, [P, IP]),
+        "hermite_batch_set_tiles": (I, [P, IP]),
+        "hermite_batch_tile_shape": (I, [I, I, IP, IP]),
         "hermite_batch_step": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "hermite_batch_run": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), I, P]),
         "hermite_set_schedule": (I, [P, I, I]),

@@ -15,26 +15,42 @@
 
 namespace hermite {
 
-// Tile shapes of the batched kernel per order (NT = 256 threads for all),
-// chosen so that the x-, y- and z-pass items split over the threads with
-// little left for a last partial chunk: at m = 3, 8 x 2 gives exactly 3, 2
-// and 1 items per thread; at m = 1, 16 x 8 gives 4.5, 4 and 2 (8 x 8: 2.25,
-// 2, 1); at m = 2, 16 x 4 gives 5.6, 4.5 and 2.25 (8 x 4: 2.8, 2.25, 1.1).
-template <int M> struct BatchTile;
-template <> struct BatchTile<2> { static constexpr int TX = 16, TY = 8; };
-template <> struct BatchTile<3> { static constexpr int TX = 16, TY = 4; };
-template <> struct BatchTile<4> { static constexpr int TX = 8, TY = 2; };
+// Tile shapes of the batched kernel, two per order (NT = 256 threads for
+// all), chosen so that the x-, y- and z-pass items split over the threads with
+// little left for a last partial chunk.  Items per thread (x, y, z pass):
+//   m = 1: 16 x 8 -> 4.5, 4, 2;      8 x 8 -> 2.25, 2, 1
+//   m = 2: 16 x 4 -> 5.6, 4.5, 2.25; 8 x 4 -> 2.8, 2.25, 1.1
+//   m = 3:  8 x 2 -> 3, 2, 1;        4 x 4 -> 2.5, 2, 1
+// Every second shape needs less shared memory than the largest first one, so
+// offering it costs no occupancy.  The per-node arithmetic of the tile body
+// does not depend on the shape, so every shape gives the same bits.
+template <int M, int K> struct BatchTile;
+template <> struct BatchTile<2, 0> { static constexpr int TX = 16, TY = 8; };
+template <> struct BatchTile<2, 1> { static constexpr int TX = 8, TY = 8; };
+template <> struct BatchTile<3, 0> { static constexpr int TX = 16, TY = 4; };
+template <> struct BatchTile<3, 1> { static constexpr int TX = 8, TY = 4; };
+template <> struct BatchTile<4, 0> { static constexpr int TX = 8, TY = 2; };
+template <> struct BatchTile<4, 1> { static constexpr int TX = 4, TY = 4; };
 constexpr int kBatchThreads = 256;
 // Resident CTAs per SM the compiler must fit the batched kernel's registers to.
 #ifndef HERMITE_BATCH_MIN_BLOCKS
 #define HERMITE_BATCH_MIN_BLOCKS 2
 #endif
 
-void batch_tile_shape(int m, int *tx, int *ty) {
-  switch (m) {
-    case 1: *tx = BatchTile<2>::TX; *ty = BatchTile<2>::TY; break;
-    case 2: *tx = BatchTile<3>::TX; *ty = BatchTile<3>::TY; break;
-    default: *tx = BatchTile<4>::TX; *ty = BatchTile<4>::TY; break;
+template <int M, int K>
+static void shape_of(int *tx, int *ty) {
+  *tx = BatchTile<M, K>::TX;
+  *ty = BatchTile<M, K>::TY;
+}
+
+void batch_tile_shape(int m, int k, int *tx, int *ty) {
+  switch (m * kBatchShapes + (k == 1 ? 1 : 0)) {
+    case 1 * kBatchShapes + 0: shape_of<2, 0>(tx, ty); break;
+    case 1 * kBatchShapes + 1: shape_of<2, 1>(tx, ty); break;
+    case 2 * kBatchShapes + 0: shape_of<3, 0>(tx, ty); break;
+    case 2 * kBatchShapes + 1: shape_of<3, 1>(tx, ty); break;
+    case 3 * kBatchShapes + 1: shape_of<4, 1>(tx, ty); break;
+    default: shape_of<4, 0>(tx, ty); break;
   }
 }
 
@@ -73,19 +89,39 @@ constexpr size_t batch_tables_bytes() {  // the record in shared memory, 16-byte
   return (batch_record_bytes<TC>() + 15) / 16 * 16;
 }
 
-template <typename TC>
-constexpr size_t batch_smem_bytes() {
-  constexpr size_t a = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>::SMEM;
-  constexpr size_t b = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>::SMEM;
-  constexpr size_t c = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>::SMEM;
-  constexpr size_t mx = a > b ? (a > c ? a : c) : (b > c ? b : c);
-  return mx + batch_tables_bytes<TC>();
+template <typename TC, int M, int K>
+constexpr size_t shape_smem() {
+  return FusedShape<TC, M, BatchTile<M, K>::TX, BatchTile<M, K>::TY>::SMEM;
 }
 
-template <typename TS, typename TC, int M>
-__device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
-                                           const PackedCoeffs *pc, TC *sX, TC *sY, int s) {
-  constexpr int TX = BatchTile<M>::TX, TY = BatchTile<M>::TY;
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
+template <typename TC>
+constexpr size_t batch_smem_bytes() {
+  return cmax(cmax(cmax(shape_smem<TC, 2, 0>(), shape_smem<TC, 2, 1>()),
+                   cmax(shape_smem<TC, 3, 0>(), shape_smem<TC, 3, 1>())),
+              cmax(shape_smem<TC, 4, 0>(), shape_smem<TC, 4, 1>())) +
+         batch_tables_bytes<TC>();
+}
+
+static_assert(shape_smem<float, 2, 1>() <= shape_smem<float, 3, 0>() &&
+                  shape_smem<float, 3, 1>() <= shape_smem<float, 3, 0>() &&
+                  shape_smem<float, 4, 1>() <= shape_smem<float, 3, 0>(),
+              "the second shapes must not raise the batched kernel's shared memory");
+
+// Each (order, shape) body is its own function: inlined into one kernel the
+// six bodies share one register allocation and spill inside the tile loops.
+#ifdef HERMITE_BATCH_INLINE
+#define HERMITE_BATCH_TILE_FN __forceinline__
+#else
+#define HERMITE_BATCH_TILE_FN __noinline__
+#endif
+
+template <typename TS, typename TC, int M, int K>
+__device__ HERMITE_BATCH_TILE_FN void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
+                                           const PackedCoeffs *pc, TC *sX, int s) {
+  constexpr int TX = BatchTile<M, K>::TX, TY = BatchTile<M, K>::TY;
+  using Sh = FusedShape<TC, M, TX, TY>;
   Geom g;
   g.nx = sm.n[0];
   g.ny = sm.n[1];
@@ -97,7 +133,7 @@ __device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &
   const int x0 = (it.tile % tiles_x) * TX, y0 = (it.tile / tiles_x) * TY;
   const int z0 = it.z0, z1 = min(it.z0 + sm.zchunk, g.nz);
   fused_tile<TS, TC, M, TX, TY, kBatchThreads, 2, kBatchPacked<TC>, kBatchPacked<TC>>(
-      (const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sY, pc);
+      (const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sX + Sh::SX, pc);
 }
 
 template <typename TS, typename TC>
@@ -124,22 +160,14 @@ __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
       for (int k = threadIdx.x; k < (int)(batch_record_bytes<TC>() / 8); k += kBatchThreads) dst[k] = src[k];
     }
     __syncthreads();
-    switch (sm.m) {
-      case 1: {
-        using Sh = FusedShape<TC, 2, BatchTile<2>::TX, BatchTile<2>::TY>;
-        batch_tile<TS, TC, 2>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
-        break;
-      }
-      case 2: {
-        using Sh = FusedShape<TC, 3, BatchTile<3>::TX, BatchTile<3>::TY>;
-        batch_tile<TS, TC, 3>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
-        break;
-      }
-      default: {
-        using Sh = FusedShape<TC, 4, BatchTile<4>::TX, BatchTile<4>::TY>;
-        batch_tile<TS, TC, 4>(sm, it, *sco, spc, sX, sX + Sh::SX, s);
-        break;
-      }
+    switch (sm.m * kBatchShapes + sm.shape) {
+      case 1 * kBatchShapes + 0: batch_tile<TS, TC, 2, 0>(sm, it, *sco, spc, sX, s); break;
+      case 1 * kBatchShapes + 1: batch_tile<TS, TC, 2, 1>(sm, it, *sco, spc, sX, s); break;
+      case 2 * kBatchShapes + 0: batch_tile<TS, TC, 3, 0>(sm, it, *sco, spc, sX, s); break;
+      case 2 * kBatchShapes + 1: batch_tile<TS, TC, 3, 1>(sm, it, *sco, spc, sX, s); break;
+      case 3 * kBatchShapes + 0: batch_tile<TS, TC, 4, 0>(sm, it, *sco, spc, sX, s); break;
+      case 3 * kBatchShapes + 1: batch_tile<TS, TC, 4, 1>(sm, it, *sco, spc, sX, s); break;
+      default: break;  // the host builds only the pairs above
     }
     __syncthreads();  // every thread is done with sco, sX, sY and s_item
   }

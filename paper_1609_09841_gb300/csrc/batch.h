@@ -13,7 +13,7 @@ struct BatchSim {      // one simulation of a batch, as the kernel sees it
   int n[3];            // nodes along x1, x2, x3
   int m;               // order
   int zchunk;          // cells per work item along x3
-  int pad;
+  int shape;           // tile shape index of this order, 0 .. kBatchShapes-1
 };
 
 struct BatchItem {     // one unit of work: a TX x TY x zchunk block of one simulation
@@ -23,7 +23,8 @@ struct BatchItem {     // one unit of work: a TX x TY x zchunk block of one simu
   int pad;
 };
 
-void batch_tile_shape(int m, int *tx, int *ty);
+constexpr int kBatchShapes = 2;  // tile shapes compiled per order
+void batch_tile_shape(int m, int shape, int *tx, int *ty);
 // One simulation's table record as the kernel reads it (compute kF32:
 // StepCoeffs<float> then its PackedCoeffs; kF64: StepCoeffs<double>).
 size_t batch_coeff_record_bytes(int compute);

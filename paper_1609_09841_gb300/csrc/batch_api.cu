@@ -33,6 +33,7 @@ struct BatchPlan {
   std::vector<int> n;           // 3 per simulation
   std::vector<size_t> elems;
   int zchunk[4] = {0, 16, 16, 16};  // per order
+  int shape[4] = {0, 0, 0, 0};      // tile shape index per order (batch_tile_shape)
   void *coeffs = nullptr;       // device table records, one per simulation (batch_write_record)
   BatchItem *items = nullptr;   // device work list
   int nitems = 0;
@@ -72,7 +73,7 @@ int build_items(BatchPlan *b) {
     for (int i = 0; i < b->nsims; ++i) {
       if (b->m[i] != order) continue;
       int tx, ty;
-      batch_tile_shape(order, &tx, &ty);
+      batch_tile_shape(order, b->shape[order], &tx, &ty);
       const int *n = &b->n[3 * i];
       const int tiles = ((n[0] + tx - 1) / tx) * ((n[1] + ty - 1) / ty);
       b->zc[i] = b->zchunk[order];
@@ -117,7 +118,8 @@ int get_set(BatchPlan *b, const void *const *in, void *const *out, BatchSim **de
       cudaGetLastError();
       return fail(HERMITE_EINVAL, "states of simulation %d must be device memory", i);
     }
-    host[i] = BatchSim{in[i], out[i], {b->n[3 * i], b->n[3 * i + 1], b->n[3 * i + 2]}, b->m[i], b->zc[i], 0};
+    host[i] = BatchSim{in[i], out[i], {b->n[3 * i], b->n[3 * i + 1], b->n[3 * i + 2]}, b->m[i], b->zc[i],
+                       b->shape[b->m[i]]};
   }
   DescSet s;
   s.in.assign(in, in + b->nsims);
@@ -225,6 +227,22 @@ int hermite_batch_set_schedule(hermite_plan_t p, const int zchunk[3]) {
     if (zchunk[k] < 1 || zchunk[k] > 4096) return fail(HERMITE_EINVAL, "zchunk[%d] = %d out of range", k, zchunk[k]);
   for (int k = 0; k < 3; ++k) p->batch->zchunk[k + 1] = zchunk[k];
   return build_items(p->batch);
+}
+
+int hermite_batch_set_tiles(hermite_plan_t p, const int tile[3]) {
+  if (!p || !p->batch || !tile) return fail(HERMITE_EINVAL, "not a batched plan");
+  for (int k = 0; k < 3; ++k)
+    if (tile[k] < 0 || tile[k] >= kBatchShapes)
+      return fail(HERMITE_EINVAL, "tile[%d] = %d out of range [0, %d)", k, tile[k], kBatchShapes);
+  for (int k = 0; k < 3; ++k) p->batch->shape[k + 1] = tile[k];
+  return build_items(p->batch);
+}
+
+int hermite_batch_tile_shape(int m, int tile, int *tx, int *ty) {
+  if (m < 1 || m > 3 || tile < 0 || tile >= kBatchShapes || !tx || !ty)
+    return fail(HERMITE_EINVAL, "no batched tile shape %d for order %d", tile, m);
+  batch_tile_shape(m, tile, tx, ty);
+  return HERMITE_OK;
 }
 
 int hermite_batch_step(hermite_plan_t p, const void *const *in, void *const *out, int parity, void *stream) {

@@ -143,6 +143,23 @@ def test_batched_plan_rejected_by_single_calls_without_gpu(capi):
     assert not p.value
 
 
+def test_batch_tile_shapes_without_gpu(capi):
+    """The batched kernel's two tile shapes per order, and the range checks of
+    hermite_batch_tile_shape / hermite_batch_set_tiles."""
+    want = {(1, 0): (16, 8), (1, 1): (8, 8), (2, 0): (16, 4), (2, 1): (8, 4), (3, 0): (8, 2), (3, 1): (4, 4)}
+    tx, ty = ctypes.c_int(), ctypes.c_int()
+    for (m, t), shape in want.items():
+        assert capi.lib.hermite_batch_tile_shape(m, t, ctypes.byref(tx), ctypes.byref(ty)) == 0
+        assert (tx.value, ty.value) == shape
+    for m, t in ((0, 0), (4, 0), (1, -1), (2, 2)):
+        assert capi.lib.hermite_batch_tile_shape(m, t, ctypes.byref(tx), ctypes.byref(ty)) == -1
+    assert capi.lib.hermite_batch_set_tiles(None, (ctypes.c_int * 3)(0, 0, 0)) == -1
+    rc, p = _plan(capi)
+    assert rc == 0
+    assert capi.lib.hermite_batch_set_tiles(p, (ctypes.c_int * 3)(0, 0, 0)) == -1   # not a batched plan
+    capi.lib.hermite_destroy(p)
+
+
 def test_taylor_order_validation(capi):
     rc, p = _plan(capi, m=2)
     assert rc == 0

@@ -1,4 +1,6 @@
 """Batched half steps (one persistent launch per half step, CUDA-graph runs)."""
+import json
+
 import numpy as np
 import pytest
 
@@ -32,13 +34,15 @@ def _sims(spec, c=1.0, lam=0.2):
     return out
 
 
-@pytest.mark.parametrize("zchunk", [(16, 16, 16), (3, 2, 1)])
-def test_batch_step_matches_oracle_fp64(torch_cuda, zchunk):
+@pytest.mark.parametrize("zchunk,tiles", [((16, 16, 16), (0, 0, 0)), ((3, 2, 1), (0, 0, 0)),
+                                         ((16, 16, 16), (1, 1, 1)), ((5, 1, 2), (1, 0, 1))])
+def test_batch_step_matches_oracle_fp64(torch_cuda, zchunk, tiles):
     torch = torch_cuda
     from paper_1609_09841_gb300.batch import BatchPlan
     sims = _sims(SMALL, c=1.2)
     bp = BatchPlan(sims, prec="fp64", state="fp64")
     bp.set_schedule(zchunk)
+    bp.set_tiles(tiles)
     xs = [HI.random_state(s["m"], s["grid"], seed=60 + i) for i, s in enumerate(sims)]
     a = [torch.from_numpy(x).cuda() for x in xs]
     b = [torch.full_like(t, float("nan")) for t in a]
@@ -50,15 +54,17 @@ def test_batch_step_matches_oracle_fp64(torch_cuda, zchunk):
             assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (i, parity)
 
 
-def test_batch_fp32_equals_single_plans_and_graph_run(torch_cuda):
+@pytest.mark.parametrize("tiles", [(0, 0, 0), (1, 1, 1), (0, 1, 1)])
+def test_batch_fp32_equals_single_plans_and_graph_run(torch_cuda, tiles):
     """FP32: each simulation of a batched step equals its own single-grid
-    plan's step bit for bit (same per-cell arithmetic), and a 7-half-step
-    graph run equals 7 batched steps bit for bit."""
+    plan's step bit for bit (same per-cell arithmetic, whatever the tile
+    shape), and a 7-half-step graph run equals 7 batched steps bit for bit."""
     torch = torch_cuda
     from paper_1609_09841_gb300 import Plan
     from paper_1609_09841_gb300.batch import BatchPlan
     sims = _sims(SMALL)
     bp = BatchPlan(sims, prec="fp32", state="fp32")
+    bp.set_tiles(tiles)
     gen = torch.Generator(device="cuda").manual_seed(4)
     a = [torch.randn(bp.shape(i), dtype=torch.float32, device="cuda", generator=gen) for i in range(len(sims))]
     a0 = [t.clone() for t in a]
@@ -86,8 +92,8 @@ def test_batch_fp32_equals_single_plans_and_graph_run(torch_cuda):
 def test_config4_batch_64_sims(torch_cuda):
     """64 seeded simulations (sides from {32,48,64,96} per dimension, m from
     {1,2,3}, Gaussian pulses), FP32, 200 half steps as one graph, with the
-    autotuned z-chunks; every simulation equals its single-grid FP32 run bit
-    for bit and stays finite."""
+    autotuned tile shapes and z-chunks; every simulation equals its
+    single-grid FP32 run bit for bit and stays finite."""
     torch = torch_cuda
     from paper_1609_09841_gb300 import Plan
     from paper_1609_09841_gb300.autotune import tune_batch
@@ -101,9 +107,20 @@ def test_config4_batch_64_sims(torch_cuda):
     a = [torch.from_numpy(HI.gaussian_pulse(d["m"], d["n"], d["h"], d["centre"], d["sigma"])).float().cuda()
          for d in draw]
     b = [torch.empty_like(t) for t in a]
-    tune_batch(bp, [t.clone() for t in a], b)
+    tuned = tune_batch(bp, [t.clone() for t in a], b)
     res = bp.run(a, b, 200)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x, y = [t.clone() for t in a], [torch.empty_like(t) for t in a]
+    bp.run(x, y, 200)            # captures and instantiates the graph of this buffer pair
+    torch.cuda.synchronize()
+    e0.record()
+    bp.run(x, y, 200)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"config": 4, "sims": len(sims), "half_steps": 200, "tile": tuned["tile"],
+                      "zchunk": tuned["zchunk"], "ms_200_half_steps": e0.elapsed_time(e1),
+                      "tuning_ms_per_half_step": tuned["ms"]}))
     for i in (0, 17, 40, 63):
         s = sims[i]
         p = Plan(s["m"], s["grid"], s["h"], s["c"], s["dt"], prec="fp32", state="fp32")
