@@ -206,18 +206,22 @@ int hermite_debug_selftest(hermite_plan_t plan, const void *in, void *out, int p
 
 /* Device status of the plan's kernels: *status receives the OR of the flags
  * that kernels raised since the last call (0: none) and the flags are
- * cleared.  Bit 0: a CTA of the tensor-core kernel (HERMITE_3XTF32,
- * HERMITE_SPLITBF16) gave up waiting for its MMAs after its bounded wait; its
- * outputs are then incomplete.  Synchronises `stream`.  The word is allocated
- * by the first tensor-core step of the plan; make that step outside any stream
- * capture. */
+ * cleared.  Bit 0: a CTA gave up after a bounded wait, its outputs then
+ * incomplete: a CTA of the tensor-core kernel (HERMITE_3XTF32,
+ * HERMITE_SPLITBF16) waiting for its MMAs, or a CTA of a staged FP32 schedule
+ * waiting for a node plane's bulk copy.  Synchronises `stream`.  The word is
+ * allocated by the plan's first step that can raise it; make that step outside
+ * any stream capture. */
 int hermite_device_status(hermite_plan_t plan, int *status, void *stream);
 
 /* Kernel schedule of the fused half step: `tile` picks one of
  * hermite_schedule_count(plan) compiled tile shapes (cells per CTA in x1, x2
  * and threads per CTA, fixed per order and precision), `zchunk` the cells
  * each CTA marches along x3 (1..4096).  Defaults: tile 0, zchunk 16.  The
- * autotuner of the Python package times the choices on the device. */
+ * autotuner of the Python package times the choices on the device.  With
+ * FP32 arithmetic (HERMITE_FP32) tiles 6 and 7 are staged: each node plane
+ * is copied into shared memory by the bulk tensor-copy engine (TMA) while the
+ * previous plane is computed; results equal the other tiles' bit for bit. */
 int hermite_schedule_count(hermite_plan_t plan);
 int hermite_set_schedule(hermite_plan_t plan, int tile, int zchunk);
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhermite.so")
-SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu", "advect.cu", "symbol.cpp", "fused_tc.cu", "remainder.cu"]
+SOURCES = ["api.cu", "tables.cpp", "fused_f64.cu", "fused_f32.cu", "fused_f32s64.cu", "split.cu", "norms.cu", "receivers.cu", "batch.cu", "batch_api.cu", "split_static.cu", "hybrid.cu", "advect.cu", "symbol.cpp", "fused_tc.cu", "remainder.cu", "tma_map.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fno-gnu-unique: the function-local statics of template launchers (the per-device record that a
 # kernel's shared-memory limit was raised) stay private to each library, also when a process loads

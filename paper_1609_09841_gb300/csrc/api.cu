@@ -218,6 +218,21 @@ int run_adv_step(hermite_plan_s *p, const void *in, void *out, int parity, cudaS
 
 // Device-pointer half step of either direction (adjoint: transposed tables,
 // mirrored corner offset).
+// The plan's device status word (time-outs of bounded device waits), made on
+// first use and read back by hermite_device_status.
+int ensure_status(hermite_plan_s *p) {
+  if (p->status) return HERMITE_OK;
+  cudaError_t e = dev_malloc((void **)&p->status, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->status = nullptr;
+    return fail(HERMITE_ENOMEM, "device status word");
+  }
+  e = cudaMemset(p->status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "device status word");
+  return HERMITE_OK;
+}
+
 int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode, cudaStream_t st, int zlo = 0,
              int zhi = -1) {
   if (int rc = ensure_dbg(p)) return rc;
@@ -249,16 +264,7 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
       return HERMITE_OK;
     }
     if (is_tc_prec(p->prec)) {
-      if (!p->status) {
-        cudaError_t ea = dev_malloc((void **)&p->status, sizeof(int));
-        if (ea != cudaSuccess) {
-          cudaGetLastError();
-          p->status = nullptr;
-          return fail(HERMITE_ENOMEM, "device status word");
-        }
-        ea = cudaMemset(p->status, 0, sizeof(int));
-        if (ea != cudaSuccess) return cuda_fail(ea, "device status word");
-      }
+      if (int rc = ensure_status(p)) return rc;
       const TcBTable &bt = mode == kAdjoint ? p->tc_adj : (mode == kDc ? p->tc_dc : p->tc_fwd);
       e = launch_fused_tc(p->prec == HERMITE_3XTF32 ? 0 : 1, p->m, p->state == HERMITE_STATE_FP64 ? kF64 : kF32, in,
                           out, g, cf, bt, p->zchunk, p->status, st);
@@ -269,12 +275,18 @@ int run_step(hermite_plan_s *p, const void *in, void *out, int parity, int mode,
     if (p->prec == HERMITE_FP64)
       e = rk4 ? launch_fused_f64(p->m, p->tile, (const double *)in, (double *)out, g, cd, p->zchunk, st)
               : launch_fused_f64_fullq(p->m, (const double *)in, (double *)out, g, cd, p->zchunk, st);
-    else if (p->state == HERMITE_STATE_FP64)
-      e = rk4 ? launch_fused_f32_s64(p->m, p->tile, (const double *)in, (double *)out, g, cf, p->zchunk, st)
-              : launch_fused_f32_fullq(p->m, kF64, in, out, g, cf, p->zchunk, st);
-    else
-      e = rk4 ? launch_fused_f32_s32(p->m, p->tile, (const float *)in, (float *)out, g, cf, p->zchunk, st)
-              : launch_fused_f32_fullq(p->m, kF32, in, out, g, cf, p->zchunk, st);
+    else {
+      if (rk4 && p->tile >= kFirstStagedTile)
+        if (int rc = ensure_status(p)) return rc;
+      if (p->state == HERMITE_STATE_FP64)
+        e = rk4 ? launch_fused_f32_s64(p->m, p->tile, (const double *)in, (double *)out, g, cf, p->zchunk, p->status,
+                                       st)
+                : launch_fused_f32_fullq(p->m, kF64, in, out, g, cf, p->zchunk, st);
+      else
+        e = rk4 ? launch_fused_f32_s32(p->m, p->tile, (const float *)in, (float *)out, g, cf, p->zchunk, p->status,
+                                       st)
+                : launch_fused_f32_fullq(p->m, kF32, in, out, g, cf, p->zchunk, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "fused half-step launch");
     return HERMITE_OK;
   }

@@ -23,6 +23,14 @@
 // cell below it (completed and stored) and the cell above it (kept in
 // registers until the next plane).  Two barriers per plane.  Every per-item
 // index is computed once before the march.
+//
+// Staged schedules (ST) stage each node plane in shared memory first: one
+// tiled bulk tensor copy (TMA) per plane brings the (TY + 1) x BW window of
+// every coefficient row, issued by one thread right after the x-pass of the
+// previous plane and completed on an mbarrier while that plane's y- and
+// z-passes run; the x-pass then reads its node pairs from shared memory.
+// Tiles whose window wraps around the periodic boundary, and grids whose row
+// pitch the copy engine cannot address, fill the same buffer with plain loads.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,8 +40,43 @@
 
 #include "hermite_impl.h"
 #include "packed_f32.cuh"
+#include "tma_ptx.cuh"
 
 namespace hermite {
+
+// Staging of the x-pass input (ST schedules).  U: state elements per 16
+// bytes (the copy engine's alignment of the innermost coordinate); the window
+// of a tile starts at xa, x0 + s rounded down to a multiple of U, and is BW
+// columns wide: TX + 1 nodes after an offset of at most U - 1, rounded up to
+// a multiple of U.
+template <typename TS, int M, int TX, int TY>
+struct StageShape {
+  static constexpr int U = 16 / (int)sizeof(TS);
+  static constexpr int BW = (TX + 2 * U - 1) / U * U;
+  static constexpr int ROWS = TY + 1;
+  static constexpr int NC = 2 * M * M * M;    // coefficient rows of both fields
+  static constexpr int BCS = ROWS * BW;       // elements of one coefficient row's window
+  static constexpr int ELEMS = NC * BCS;
+  static constexpr size_t BYTES = ((size_t)ELEMS * sizeof(TS) + 127) / 128 * 128;
+  static constexpr size_t TAB_BYTES = ((size_t)BCS * sizeof(int) + 15) / 16 * 16;
+  // dynamic shared memory beyond the fused tile's: 128-byte alignment slack,
+  // the buffer and the in-plane offsets of the plain-load fill
+  static constexpr size_t EXTRA = 128 + BYTES + TAB_BYTES;
+};
+
+template <typename TS>
+struct StageArgs {
+  const CUtensorMap *map;  // the input state as a tensor (valid if map_ok)
+  TS *buf;                 // StageShape::ELEMS elements, 128-byte aligned
+  int *tab;                // StageShape::BCS in-plane offsets (plain-load fill)
+  uint64_t *mbar;          // one mbarrier, phase p completes with plane p
+  int *status;             // bit 0 set when a copy did not complete in time
+  int map_ok;
+};
+
+// Polls of a staged plane's mbarrier before the CTA gives up (each poll may
+// suspend the thread for a while): far beyond any copy's latency.
+constexpr uint32_t kStageMaxPolls = 1u << 21;
 
 // L1 prefetch hint (PTX prefetch.global.L1): fetches the line holding p into
 // L1 without a register result.  Callers pass addresses they later load.
@@ -146,12 +189,16 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // PF: prefetch the next plane's x-pass lines into L1 during the y- and
 // z-passes.  The batched kernel uses it; the single-grid kernels measured
 // slower with it (and with the same hint into L2) and do not.
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, bool PF = false>
+// ST: staged x-pass input (StageArgs `stg`); returns early, with bit 0 of
+// *stg->status set, if a plane's copy does not complete within the poll limit.
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, bool PF = false,
+          bool ST = false>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
                                            TC *__restrict__ sX, TC *__restrict__ sY,
-                                           const PackedCoeffs *pc = nullptr) {
+                                           const PackedCoeffs *pc = nullptr, const StageArgs<TS> *stg = nullptr) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
+  using Sg = StageShape<TS, M, TX, TY>;
   constexpr int NYN = Sh::NYN, NA = Sh::NA, NG = Sh::NG;
   constexpr int XPT = (Sh::XITEMS + NT - 1) / NT;
   constexpr int YPT = (Sh::YITEMS + NT - 1) / NT;
@@ -162,7 +209,16 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   const size_t pxy = (size_t)nx * ny;
   const size_t plane = pxy * nz;
 
-  // x-items: source planes and in-plane offsets of the edge's two nodes.
+  // Staged input window: first column xa (x0 + s rounded down to a multiple
+  // of U) and the tile's offset in it; copied by the engine when the window
+  // lies inside the grid, else filled with plain loads (wrapping).
+  const int xs0 = x0 + s;
+  const int xa = xs0 >= 0 ? xs0 / Sg::U * Sg::U : -((-xs0 + Sg::U - 1) / Sg::U) * Sg::U;
+  bool use_tma = false;
+  if constexpr (ST) use_tma = stg->map_ok && xa >= 0 && xa + Sg::BW <= nx && y0 + s >= 0 && y0 + s + TY < ny;
+
+  // x-items: source planes and in-plane offsets of the edge's two nodes
+  // (staged: xl is the left node's place in the window, xr unused).
   const TS *xsrc[XPT];
   int xl[XPT], xr[XPT], xdst[XPT];
 #pragma unroll
@@ -174,12 +230,42 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     const int iy = t % M; t /= M;
     const int iz = t % M;
     const int f = t / M;
-    const int gy = wrap_index(y0 + s + ey, ny);
-    xsrc[k] = in + (size_t)(((f * M + iz) * M + iy) * M) * plane;
-    xl[k] = gy * nx + wrap_index(x0 + s + ex, nx);
-    xr[k] = gy * nx + wrap_index(x0 + s + ex + 1, nx);
+    if constexpr (ST) {
+      xsrc[k] = nullptr;
+      xl[k] = ((((f * M + iz) * M + iy) * M) * Sg::ROWS + ey) * Sg::BW + (xs0 - xa) + ex;
+      xr[k] = 0;
+    } else {
+      const int gy = wrap_index(y0 + s + ey, ny);
+      xsrc[k] = in + (size_t)(((f * M + iz) * M + iy) * M) * plane;
+      xl[k] = gy * nx + wrap_index(x0 + s + ex, nx);
+      xr[k] = gy * nx + wrap_index(x0 + s + ex + 1, nx);
+    }
     xdst[k] = e < Sh::XITEMS ? ((f * M + iz) * M + iy) * Sh::XB + ey * TX + ex : -1;
   }
+  if constexpr (ST) {
+    if (use_tma) {
+      if (threadIdx.x == 0) {
+        tc::mbar_init(stg->mbar, 1);
+        tma::fence_mbar_init();
+        tma::prefetch_map(stg->map);
+      }
+    } else {
+      // in-plane offsets of the window's (row, column) pairs, wrapped
+      for (int q = threadIdx.x; q < Sg::BCS; q += NT)
+        stg->tab[q] = wrap_index(y0 + s + q / Sg::BW, ny) * nx + wrap_index(xa + q % Sg::BW, nx);
+    }
+    __syncthreads();
+  }
+  // one thread starts the copy of plane pp's window
+  auto stage_issue = [&](int pp) {
+    if constexpr (ST) {
+      tc::fence_async_smem();  // the x-pass's reads of the buffer come before the copy's writes
+      tma::arrive_expect_tx(stg->mbar, (uint32_t)(Sg::ELEMS * sizeof(TS)));
+      tma::load_4d(stg->buf, stg->map, xa, y0 + s, wrap_index(z0 + s + pp, nz), 0, stg->mbar);
+    }
+  };
+  if constexpr (ST)
+    if (use_tma && threadIdx.x == 0) stage_issue(0);
   // y-items: base of the two edges in sX and of the face in sY.
   int ysrc[YPT], ydst[YPT];
 #pragma unroll
@@ -224,14 +310,34 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     const size_t zoff = (size_t)wrap_index(z0 + s + p, nz) * pxy;
     // x-pass on the TX x (TY+1) x-edges of node plane z0 + s + p
     TC Lv[XPT][M], Rv[XPT][M];
+    bool stage_failed = false;
+    if constexpr (ST) {
+      if (use_tma) {
+        stage_failed = !tc::mbar_wait(stg->mbar, (uint32_t)(p & 1), kStageMaxPolls);
+      } else {
+        for (int e = threadIdx.x; e < Sg::ELEMS; e += NT)
+          stg->buf[e] = state_load(g, in, in + (size_t)(e / Sg::BCS) * plane + zoff + stg->tab[e % Sg::BCS]);
+        __syncthreads();
+      }
 #pragma unroll
-    for (int k = 0; k < XPT; ++k) {
-      if (xdst[k] < 0) continue;
-      const TS *src = xsrc[k] + zoff;
+      for (int k = 0; k < XPT; ++k) {
+        if (xdst[k] < 0) continue;
 #pragma unroll
-      for (int i = 0; i < M; ++i) {
-        Lv[k][i] = (TC)state_load(g, in, src + i * plane + xl[k]);
-        Rv[k][i] = (TC)state_load(g, in, src + i * plane + xr[k]);
+        for (int i = 0; i < M; ++i) {
+          Lv[k][i] = (TC)stg->buf[xl[k] + i * Sg::BCS];
+          Rv[k][i] = (TC)stg->buf[xl[k] + i * Sg::BCS + 1];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < XPT; ++k) {
+        if (xdst[k] < 0) continue;
+        const TS *src = xsrc[k] + zoff;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          Lv[k][i] = (TC)state_load(g, in, src + i * plane + xl[k]);
+          Rv[k][i] = (TC)state_load(g, in, src + i * plane + xr[k]);
+        }
       }
     }
 #pragma unroll
@@ -280,7 +386,20 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
           }
       }
     }
-    __syncthreads();
+    if constexpr (ST) {
+      if (__syncthreads_or(stage_failed)) {  // a copy never completed: give up on the tile
+        if (threadIdx.x == 0) {
+          atomicOr(stg->status, 1);
+          // the copy may still land: one more bounded wait before the shared memory is released
+          tc::mbar_wait(stg->mbar, (uint32_t)(p & 1), kStageMaxPolls);
+        }
+        __syncthreads();
+        return;
+      }
+      if (use_tma && threadIdx.x == 0 && p < z1 - z0) stage_issue(p + 1);
+    } else {
+      __syncthreads();
+    }
     if constexpr (PF) {
       // the next plane's x-pass lines into L1 while this plane's y- and
       // z-passes run (the left nodes cover all but one x-node per row)
@@ -483,6 +602,35 @@ __global__ void __launch_bounds__(NT, MINB)
 
 #undef HERMITE_FUSED_KERNEL_BODY
 
+// Staged schedules: MINB CTAs per SM, the x-pass input staged in shared
+// memory (StageShape), `map` the tensor map of `in` when map_ok.
+// Dynamic shared memory: [alignment slack][buffer][offset table][sX][sY].
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    fused_step_kernel_st(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
+                         const StepCoeffs<TC> co, const PackedFor<TC> pc, const __grid_constant__ CUtensorMap map,
+                         int map_ok, int *status) {
+  using Sh = FusedShape<TC, M, TX, TY, G>;
+  using Sg = StageShape<TS, M, TX, TY>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t mbar;
+  unsigned char *base = smem_raw + ((128u - (tc::smem_addr(smem_raw) & 127u)) & 127u);
+  const StageArgs<TS> sa{&map, reinterpret_cast<TS *>(base), reinterpret_cast<int *>(base + Sg::BYTES), &mbar,
+                         status, map_ok};
+  TC *sX = reinterpret_cast<TC *>(base + Sg::BYTES + Sg::TAB_BYTES);
+  TC *sY = sX + Sh::SX;
+  const int tiles_x = (g.nx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % tiles_x) * TX;
+  const int y0 = (blockIdx.x / tiles_x) * TY;
+  const int z0 = g.zlo + blockIdx.y * zchunk;
+  if (z0 >= g.zhi) return;
+  constexpr bool PK = std::is_same<TC, float>::value;
+  const PackedCoeffs *pp = nullptr;
+  if constexpr (PK) pp = &pc;
+  fused_tile<TS, TC, M, TX, TY, NT, G, PK, false, true>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY,
+                                                        pp, &sa);
+}
+
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, int MINB = 1>
 cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoeffs<TC> &co,
                              int zchunk, cudaStream_t st) {
@@ -502,6 +650,33 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
   PackedFor<TC> pc{};
   if constexpr (std::is_same<TC, float>::value) pc = pack_coeffs(co);
   kern<<<grid, NT, Sh::SMEM, st>>>(in, out, g, zchunk, co, pc);
+  return cudaGetLastError();
+}
+
+// Launch of a staged schedule; `status` receives bit 0 if a plane's copy timed
+// out.  Debug builds take the plain-load fill everywhere, so that every read
+// of the state goes through the bounds check.
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
+cudaError_t launch_fused_st_cfg(const TS *in, TS *out, const Geom &g, const StepCoeffs<TC> &co, int zchunk,
+                                int *status, cudaStream_t st) {
+  using Sh = FusedShape<TC, M, TX, TY, G>;
+  using Sg = StageShape<TS, M, TX, TY>;
+  constexpr size_t smem = Sh::SMEM + Sg::EXTRA;
+  auto kern = fused_step_kernel_st<TS, TC, M, TX, TY, NT, G, MINB>;
+  static SmemAttrOnce smem_once;  // per instantiation, per device
+  if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
+  if (!status) return cudaErrorInvalidValue;
+  if (zchunk <= 0) zchunk = 16;
+  zchunk = clamp_zchunk(g.zhi - g.zlo, zchunk);
+  const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+  dim3 grid(tiles, (g.zhi - g.zlo + zchunk - 1) / zchunk);
+  PackedFor<TC> pc{};
+  if constexpr (std::is_same<TC, float>::value) pc = pack_coeffs(co);
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const int map_ok = !kDebugBuild && encode_state_map(&map, in, (int)sizeof(TS), g.nx, g.ny, g.nz, Sg::NC, Sg::BW,
+                                                      Sg::ROWS);
+  kern<<<grid, NT, smem, st>>>(in, out, g, zchunk, co, pc, map, map_ok, status);
   return cudaGetLastError();
 }
 

@@ -5,8 +5,8 @@
 namespace hermite {
 
 cudaError_t launch_fused_f32_s32(int m, int tile, const float *in, float *out, const Geom &g,
-                                 const StepCoeffs<float> &co, int zchunk, cudaStream_t st) {
-  return dispatch_f32<float>(m, tile, in, out, g, co, zchunk, st);
+                                 const StepCoeffs<float> &co, int zchunk, int *status, cudaStream_t st) {
+  return dispatch_f32<float>(m, tile, in, out, g, co, zchunk, status, st);
 }
 
 cudaError_t launch_fused_f32_fullq(int m, int state, const void *in, void *out, const Geom &g,

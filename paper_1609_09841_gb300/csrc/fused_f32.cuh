@@ -5,10 +5,19 @@
 
 namespace hermite {
 
+// Tiles 6 and 7 of every order are staged schedules (x-pass input copied
+// into shared memory by the copy engine, launch_fused_st_cfg); `status`
+// receives their copy time-outs.
 template <typename TS>
 cudaError_t dispatch_f32(int m, int tile, const TS *in, TS *out, const Geom &g, const StepCoeffs<float> &co,
-                         int zchunk, cudaStream_t st) {
+                         int zchunk, int *status, cudaStream_t st) {
   switch (m * 8 + tile) {
+    case 8 + 6: return launch_fused_st_cfg<TS, float, 2, 16, 8, 512, 2, 2>(in, out, g, co, zchunk, status, st);
+    case 8 + 7: return launch_fused_st_cfg<TS, float, 2, 8, 8, 256, 2, 4>(in, out, g, co, zchunk, status, st);
+    case 16 + 6: return launch_fused_st_cfg<TS, float, 3, 8, 4, 288, 2, 3>(in, out, g, co, zchunk, status, st);
+    case 16 + 7: return launch_fused_st_cfg<TS, float, 3, 4, 4, 160, 2, 5>(in, out, g, co, zchunk, status, st);
+    case 24 + 6: return launch_fused_st_cfg<TS, float, 4, 8, 2, 256, 2, 2>(in, out, g, co, zchunk, status, st);
+    case 24 + 7: return launch_fused_st_cfg<TS, float, 4, 4, 4, 256, 2, 2>(in, out, g, co, zchunk, status, st);
     case 8 + 0: return launch_fused_cfg<TS, float, 2, 16, 8, 512>(in, out, g, co, zchunk, st);
     case 8 + 1: return launch_fused_cfg<TS, float, 2, 8, 8, 256>(in, out, g, co, zchunk, st);
     case 8 + 2: return launch_fused_cfg<TS, float, 2, 32, 4, 512>(in, out, g, co, zchunk, st);

@@ -8,7 +8,7 @@ namespace hermite {
 
 int fused_tile_count(int prec, int m) {
   (void)m;
-  return prec == 0 ? 5 : 6;
+  return prec == 0 ? 5 : 8;  // FP32: 6 plain + 2 staged
 }
 
 cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,

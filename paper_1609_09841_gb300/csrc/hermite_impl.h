@@ -192,12 +192,15 @@ cudaError_t launch_fused_f32_fullq(int m, int state, const void *in, void *out, 
                                    const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
 // `tile` selects one of fused_tile_count(prec, m) compiled tile shapes.
 int fused_tile_count(int prec, int m);
+constexpr int kFirstStagedTile = 6;  // FP32 arithmetic: tiles 6 and 7 are staged
 cudaError_t launch_fused_f64(int m, int tile, const double *in, double *out, const Geom &g,
                              const StepCoeffs<double> &co, int zchunk, cudaStream_t st);
+// FP32 arithmetic: tiles 6 and 7 are staged (their copy time-outs set bit 0
+// of *status, a device word the caller owns; the other tiles ignore it).
 cudaError_t launch_fused_f32_s32(int m, int tile, const float *in, float *out, const Geom &g,
-                                 const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+                                 const StepCoeffs<float> &co, int zchunk, int *status, cudaStream_t st);
 cudaError_t launch_fused_f32_s64(int m, int tile, const double *in, double *out, const Geom &g,
-                                 const StepCoeffs<float> &co, int zchunk, cudaStream_t st);
+                                 const StepCoeffs<float> &co, int zchunk, int *status, cudaStream_t st);
 
 // Hybrid-precision fused half step (FP64 state): kind 0 = grade-0 chain in
 // FP64, kind 1 = in double-float; `tile` < hybrid_tile_count().

@@ -153,7 +153,8 @@ class Plan:
 
     def device_status(self, stream=None):
         """Flags raised by the plan's kernels since the last call (0: none),
-        then cleared; bit 0: a tensor-core CTA gave up waiting for its MMAs."""
+        then cleared; bit 0: a CTA gave up a bounded wait (a tensor-core CTA
+        waiting for its MMAs, a staged CTA waiting for a plane's copy)."""
         out = ctypes.c_int()
         capi.check(capi.lib.hermite_device_status(self.handle, ctypes.byref(out), _stream(stream)))
         return out.value
