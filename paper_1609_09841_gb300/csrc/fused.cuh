@@ -44,12 +44,14 @@
 
 namespace hermite {
 
-// Staging of the x-pass input (ST schedules).  U: state elements per 16
-// bytes (the copy engine's alignment of the innermost coordinate); the window
-// of a tile starts at xa, x0 + s rounded down to a multiple of U, and is BW
-// columns wide: TX + 1 nodes after an offset of at most U - 1, rounded up to
-// a multiple of U.
-template <typename TS, int M, int TX, int TY>
+// Staging of the x-pass input (ST schedules: ST buffers, 1 or 2).  U: state
+// elements per 16 bytes (the copy engine's alignment of the innermost
+// coordinate); the window of a tile starts at xa, x0 + s rounded down to a
+// multiple of U, and is BW columns wide: TX + 1 nodes after an offset of at
+// most U - 1, rounded up to a multiple of U.  With two buffers the copy of
+// plane p + 2 goes into the buffer plane p has just left, so each copy has
+// two planes' y- and z-passes to land.
+template <typename TS, int M, int TX, int TY, int NB = 1>
 struct StageShape {
   static constexpr int U = 16 / (int)sizeof(TS);
   static constexpr int BW = (TX + 2 * U - 1) / U * U;
@@ -57,19 +59,20 @@ struct StageShape {
   static constexpr int NC = 2 * M * M * M;    // coefficient rows of both fields
   static constexpr int BCS = ROWS * BW;       // elements of one coefficient row's window
   static constexpr int ELEMS = NC * BCS;
-  static constexpr size_t BYTES = ((size_t)ELEMS * sizeof(TS) + 127) / 128 * 128;
+  static constexpr size_t BYTES = ((size_t)ELEMS * sizeof(TS) + 127) / 128 * 128;  // one buffer
+  static constexpr int STRIDE = (int)(BYTES / sizeof(TS));                          // between buffers
   static constexpr size_t TAB_BYTES = ((size_t)BCS * sizeof(int) + 15) / 16 * 16;
   // dynamic shared memory beyond the fused tile's: 128-byte alignment slack,
-  // the buffer and the in-plane offsets of the plain-load fill
-  static constexpr size_t EXTRA = 128 + BYTES + TAB_BYTES;
+  // the buffers and the in-plane offsets of the plain-load fill
+  static constexpr size_t EXTRA = 128 + NB * BYTES + TAB_BYTES;
 };
 
 template <typename TS>
 struct StageArgs {
   const CUtensorMap *map;  // the input state as a tensor (valid if map_ok)
-  TS *buf;                 // StageShape::ELEMS elements, 128-byte aligned
+  TS *buf;                 // NB buffers of StageShape::STRIDE elements, 128-byte aligned
   int *tab;                // StageShape::BCS in-plane offsets (plain-load fill)
-  uint64_t *mbar;          // one mbarrier, phase p completes with plane p
+  uint64_t *mbar;          // one mbarrier per buffer: plane p completes phase p / NB of mbar[p % NB]
   int *status;             // bit 0 set when a copy did not complete in time
   int map_ok;
 };
@@ -189,16 +192,18 @@ __device__ __forceinline__ int wrap_index(int v, int n) {
 // PF: prefetch the next plane's x-pass lines into L1 during the y- and
 // z-passes.  The batched kernel uses it; the single-grid kernels measured
 // slower with it (and with the same hint into L2) and do not.
-// ST: staged x-pass input (StageArgs `stg`); returns early, with bit 0 of
-// *stg->status set, if a plane's copy does not complete within the poll limit.
+// ST: staged x-pass input in ST buffers (StageArgs `stg`; 0: not staged);
+// returns early, with bit 0 of *stg->status set, if a plane's copy does not
+// complete within the poll limit.
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, bool PK = false, bool PF = false,
-          bool ST = false>
+          int ST = 0>
 __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__restrict__ out, const Geom &g,
                                            int x0, int y0, int z0, int z1, const StepCoeffs<TC> &co,
                                            TC *__restrict__ sX, TC *__restrict__ sY,
                                            const PackedCoeffs *pc = nullptr, const StageArgs<TS> *stg = nullptr) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
-  using Sg = StageShape<TS, M, TX, TY>;
+  using Sg = StageShape<TS, M, TX, TY, ST == 2 ? 2 : 1>;
+  constexpr int NB = ST == 2 ? 2 : 1;
   constexpr int NYN = Sh::NYN, NA = Sh::NA, NG = Sh::NG;
   constexpr int XPT = (Sh::XITEMS + NT - 1) / NT;
   constexpr int YPT = (Sh::YITEMS + NT - 1) / NT;
@@ -245,7 +250,8 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   if constexpr (ST) {
     if (use_tma) {
       if (threadIdx.x == 0) {
-        tc::mbar_init(stg->mbar, 1);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tc::mbar_init(stg->mbar + b, 1);
         tma::fence_mbar_init();
         tma::prefetch_map(stg->map);
       }
@@ -256,16 +262,18 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     }
     __syncthreads();
   }
-  // one thread starts the copy of plane pp's window
+  // one thread starts the copy of plane pp's window into buffer pp % NB
   auto stage_issue = [&](int pp) {
     if constexpr (ST) {
+      uint64_t *mb = stg->mbar + pp % NB;
       tc::fence_async_smem();  // the x-pass's reads of the buffer come before the copy's writes
-      tma::arrive_expect_tx(stg->mbar, (uint32_t)(Sg::ELEMS * sizeof(TS)));
-      tma::load_4d(stg->buf, stg->map, xa, y0 + s, wrap_index(z0 + s + pp, nz), 0, stg->mbar);
+      tma::arrive_expect_tx(mb, (uint32_t)(Sg::ELEMS * sizeof(TS)));
+      tma::load_4d(stg->buf + (pp % NB) * Sg::STRIDE, stg->map, xa, y0 + s, wrap_index(z0 + s + pp, nz), 0, mb);
     }
   };
   if constexpr (ST)
-    if (use_tma && threadIdx.x == 0) stage_issue(0);
+    if (use_tma && threadIdx.x == 0)
+      for (int pp = 0; pp < NB && pp <= z1 - z0; ++pp) stage_issue(pp);
   // y-items: base of the two edges in sX and of the face in sY.
   int ysrc[YPT], ydst[YPT];
 #pragma unroll
@@ -312,11 +320,12 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     TC Lv[XPT][M], Rv[XPT][M];
     bool stage_failed = false;
     if constexpr (ST) {
+      TS *bp = stg->buf + (p % NB) * Sg::STRIDE;
       if (use_tma) {
-        stage_failed = !tc::mbar_wait(stg->mbar, (uint32_t)(p & 1), kStageMaxPolls);
+        stage_failed = !tc::mbar_wait(stg->mbar + p % NB, (uint32_t)((p / NB) & 1), kStageMaxPolls);
       } else {
         for (int e = threadIdx.x; e < Sg::ELEMS; e += NT)
-          stg->buf[e] = state_load(g, in, in + (size_t)(e / Sg::BCS) * plane + zoff + stg->tab[e % Sg::BCS]);
+          bp[e] = state_load(g, in, in + (size_t)(e / Sg::BCS) * plane + zoff + stg->tab[e % Sg::BCS]);
         __syncthreads();
       }
 #pragma unroll
@@ -324,8 +333,8 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
         if (xdst[k] < 0) continue;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          Lv[k][i] = (TC)stg->buf[xl[k] + i * Sg::BCS];
-          Rv[k][i] = (TC)stg->buf[xl[k] + i * Sg::BCS + 1];
+          Lv[k][i] = (TC)bp[xl[k] + i * Sg::BCS];
+          Rv[k][i] = (TC)bp[xl[k] + i * Sg::BCS + 1];
         }
       }
     } else {
@@ -390,13 +399,14 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
       if (__syncthreads_or(stage_failed)) {  // a copy never completed: give up on the tile
         if (threadIdx.x == 0) {
           atomicOr(stg->status, 1);
-          // the copy may still land: one more bounded wait before the shared memory is released
-          tc::mbar_wait(stg->mbar, (uint32_t)(p & 1), kStageMaxPolls);
+          // copies may still land: one more bounded wait on each before the shared memory is released
+          for (int q = p; q < p + NB && q <= z1 - z0; ++q)
+            tc::mbar_wait(stg->mbar + q % NB, (uint32_t)((q / NB) & 1), kStageMaxPolls);
         }
         __syncthreads();
         return;
       }
-      if (use_tma && threadIdx.x == 0 && p < z1 - z0) stage_issue(p + 1);
+      if (use_tma && threadIdx.x == 0 && p + NB <= z1 - z0) stage_issue(p + NB);
     } else {
       __syncthreads();
     }
@@ -602,22 +612,22 @@ __global__ void __launch_bounds__(NT, MINB)
 
 #undef HERMITE_FUSED_KERNEL_BODY
 
-// Staged schedules: MINB CTAs per SM, the x-pass input staged in shared
-// memory (StageShape), `map` the tensor map of `in` when map_ok.
-// Dynamic shared memory: [alignment slack][buffer][offset table][sX][sY].
-template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
+// Staged schedules: MINB CTAs per SM, the x-pass input staged in NB shared
+// buffers (StageShape), `map` the tensor map of `in` when map_ok.
+// Dynamic shared memory: [alignment slack][buffers][offset table][sX][sY].
+template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB, int NB>
 __global__ void __launch_bounds__(NT, MINB)
     fused_step_kernel_st(const TS *__restrict__ in, TS *__restrict__ out, const Geom g, int zchunk,
                          const StepCoeffs<TC> co, const PackedFor<TC> pc, const __grid_constant__ CUtensorMap map,
                          int map_ok, int *status) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
-  using Sg = StageShape<TS, M, TX, TY>;
+  using Sg = StageShape<TS, M, TX, TY, NB>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar[NB];
   unsigned char *base = smem_raw + ((128u - (tc::smem_addr(smem_raw) & 127u)) & 127u);
-  const StageArgs<TS> sa{&map, reinterpret_cast<TS *>(base), reinterpret_cast<int *>(base + Sg::BYTES), &mbar,
+  const StageArgs<TS> sa{&map, reinterpret_cast<TS *>(base), reinterpret_cast<int *>(base + NB * Sg::BYTES), mbar,
                          status, map_ok};
-  TC *sX = reinterpret_cast<TC *>(base + Sg::BYTES + Sg::TAB_BYTES);
+  TC *sX = reinterpret_cast<TC *>(base + NB * Sg::BYTES + Sg::TAB_BYTES);
   TC *sY = sX + Sh::SX;
   const int tiles_x = (g.nx + TX - 1) / TX;
   const int x0 = (blockIdx.x % tiles_x) * TX;
@@ -627,8 +637,8 @@ __global__ void __launch_bounds__(NT, MINB)
   constexpr bool PK = std::is_same<TC, float>::value;
   const PackedCoeffs *pp = nullptr;
   if constexpr (PK) pp = &pc;
-  fused_tile<TS, TC, M, TX, TY, NT, G, PK, false, true>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY,
-                                                        pp, &sa);
+  fused_tile<TS, TC, M, TX, TY, NT, G, PK, false, NB>(in, out, g, x0, y0, z0, min(z0 + zchunk, g.zhi), co, sX, sY,
+                                                       pp, &sa);
 }
 
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G = 2, int MINB = 1>
@@ -654,15 +664,18 @@ cudaError_t launch_fused_cfg(const TS *in, TS *out, const Geom &g, const StepCoe
 }
 
 // Launch of a staged schedule; `status` receives bit 0 if a plane's copy timed
-// out.  Debug builds take the plain-load fill everywhere, so that every read
-// of the state goes through the bounds check.
+// out.  Two buffers when MINB CTAs with two still fit an SM's shared memory
+// (228 KB, 1 KB of it reserved per CTA), else one.  Debug builds take the
+// plain-load fill everywhere, so that every read of the state goes through
+// the bounds check.
 template <typename TS, typename TC, int M, int TX, int TY, int NT, int G, int MINB>
 cudaError_t launch_fused_st_cfg(const TS *in, TS *out, const Geom &g, const StepCoeffs<TC> &co, int zchunk,
                                 int *status, cudaStream_t st) {
   using Sh = FusedShape<TC, M, TX, TY, G>;
-  using Sg = StageShape<TS, M, TX, TY>;
+  constexpr int NB = (Sh::SMEM + StageShape<TS, M, TX, TY, 2>::EXTRA + 1024) * MINB <= 228 * 1024 ? 2 : 1;
+  using Sg = StageShape<TS, M, TX, TY, NB>;
   constexpr size_t smem = Sh::SMEM + Sg::EXTRA;
-  auto kern = fused_step_kernel_st<TS, TC, M, TX, TY, NT, G, MINB>;
+  auto kern = fused_step_kernel_st<TS, TC, M, TX, TY, NT, G, MINB, NB>;
   static SmemAttrOnce smem_once;  // per instantiation, per device
   if (cudaError_t e = raise_smem_limit(smem_once, kern, smem); e != cudaSuccess) return e;
   if (!status) return cudaErrorInvalidValue;
