@@ -28,10 +28,20 @@ __device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {  // requires
 // Split a double into hi + lo without FP64 arithmetic: hi keeps the top 24
 // significand bits (exact in FP32), lo the remaining 29 bits rounded to FP32
 // (scaled by the exponent; values below 2^-74 keep hi only).  The pair is
-// accurate to about 2^-47 relative.
+// accurate to about 2^-47 relative.  hi is assembled from the bits (sign,
+// exponent rebiased from 1023 to 127, the top 23 stored significand bits)
+// when it is a normal FP32 number, which keeps the conversion off the FP64
+// pipe; outside that range (zero, tiny, huge, non-finite) the masked double
+// is converted, to the same value.
 __device__ __forceinline__ df32 df_from(double x) {
   const long long b = __double_as_longlong(x);
-  const float hi = __double2float_rn(__longlong_as_double(b & ~0x1FFFFFFFLL));
+  const unsigned bh = (unsigned)((unsigned long long)b >> 32), bl = (unsigned)b;
+  const int ef = (int)((bh >> 20) & 0x7FFu) - 1023 + 127;  // biased FP32 exponent of x
+  float hi;
+  if (ef >= 1 && ef <= 254)
+    hi = __uint_as_float((bh & 0x80000000u) | ((unsigned)ef << 23) | (__funnelshift_r(bl, bh, 29) & 0x7FFFFFu));
+  else
+    hi = __double2float_rn(__longlong_as_double(b & ~0x1FFFFFFFLL));
   const int e = (int)((b >> 52) & 0x7FF) - 1075;  // weight of the last significand bit is 2^e
   float lo = 0.f;
   if (e >= -126) {
