@@ -236,6 +236,10 @@ struct RemCoeffs {
   // the same as pairs of rows (r, r+1) = (2 rp, 2 rp + 1) for fma.rn.f32x2 (low word row 2 rp)
   unsigned long long gy2[3][2][4];        // [b][rp][i]
   unsigned long long kz2[2][2][2][2][4];  // [fo][fi][g - 1][rp][i]
+  unsigned long long rr2[3][3][2][4];     // [d][a][rp][i]: rows (2 rp, 2 rp + 1) of rr[d][a]
+  // the remainder's -C(j, i) and the Taylor shift's C(j, r) 2^-(j-r), each in both words
+  unsigned long long edge2[4][4];         // [i][j], j >= i
+  unsigned long long ts02[4][4];          // [r][j], j > r
 };
 void build_rem_coeffs(int m, const double h[3], double c, double tau, const StepCoeffs<float> &f32,
                       RemCoeffs *out);

@@ -50,16 +50,6 @@ namespace hermite {
 // remainder with row sums <= 7: 27 * 2^18 < 2^24).
 constexpr int kRemBitsIn = 18;
 
-__host__ __device__ constexpr int binom_c(int n, int k) {
-  int r = 1;
-  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
-  return (k < 0 || k > n) ? 0 : r;
-}
-// C(j, r) 2^-(j-r): coefficient of xi^r of (xi + 1/2)^j.
-__host__ __device__ constexpr float ts0_c(int r, int j) {
-  return j < r ? 0.f : (float)binom_c(j, r) / (float)(1 << (j - r));
-}
-
 // The split constant of a grid: for |x| <= m, C = 1.5 * 2^(E - B + 23) with
 // 2^E > m, so that (x + C) - C rounds x to a multiple of 2^(E - B).
 template <int B>
@@ -77,28 +67,26 @@ __device__ __forceinline__ unsigned long long grid_split(float hi, float lo, flo
 }
 
 // Remainder and Taylor shift of one edge whose left and right data are the
-// grid-split pairs Lp[j], Rp[i]:  rho_i (pairs) and TS_0 L (pairs).
+// grid-split pairs Lp[j], Rp[i]:  rho_i (pairs) and TS_0 L (pairs).  The
+// coefficients come as pairs from the tables (e2[i][j] = -C(j, i), t2[r][j] =
+// C(j, r) 2^-(j-r) in both words), so that each fma.rn.f32x2 reads its pair
+// as one operand.
 template <int M>
 __device__ __forceinline__ void rem_edge(const unsigned long long (&Lp)[M], const unsigned long long (&Rp)[M],
+                                         const unsigned long long (&e2)[4][4], const unsigned long long (&t2)[4][4],
                                          unsigned long long (&rho)[M], unsigned long long (&x0)[M]) {
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     unsigned long long acc = Rp[i];
 #pragma unroll
-    for (int j = i; j < M; ++j) {
-      const float c = -(float)binom_c(j, i);
-      acc = fma2f(pack2f(c, c), Lp[j], acc);
-    }
+    for (int j = i; j < M; ++j) acc = fma2f(e2[i][j], Lp[j], acc);
     rho[i] = acc;
   }
 #pragma unroll
   for (int r = 0; r < M; ++r) {
     unsigned long long acc = Lp[r];
 #pragma unroll
-    for (int j = r + 1; j < M; ++j) {
-      const float c = ts0_c(r, j);
-      acc = fma2f(pack2f(c, c), Lp[j], acc);
-    }
+    for (int j = r + 1; j < M; ++j) acc = fma2f(t2[r][j], Lp[j], acc);
     x0[r] = acc;
   }
 }
@@ -137,7 +125,8 @@ __device__ __forceinline__ void rem_add_rr0(const float (&rr0)[4][4], const unsi
 // (r, r+1) share their input and go through one fma.rn.f32x2.
 template <int M, int NA>
 __device__ __forceinline__ void rem_grades(const float (&ts)[3][4][4], const float (&rr)[3][4][4],
-                                           const float (&scale)[3], const float (&Lf)[M], const float (&rf)[M],
+                                           const unsigned long long (&rr2)[3][2][4], const float (&scale)[3],
+                                           const float (&Lf)[M], const float (&rf)[M],
                                            float (&outg)[NA > 1 ? NA - 1 : 1][M]) {
 #pragma unroll
   for (int a = 1; a < NA; ++a) {
@@ -145,8 +134,7 @@ __device__ __forceinline__ void rem_grades(const float (&ts)[3][4][4], const flo
     for (int rp = 0; rp < M / 2; ++rp) {
       unsigned long long acc = 0ull;
 #pragma unroll
-      for (int i = 0; i < M; ++i)
-        acc = fma2f(pack2f(rr[a][2 * rp][i], rr[a][2 * rp + 1][i]), pack2f(rf[i], rf[i]), acc);
+      for (int i = 0; i < M; ++i) acc = fma2f(rr2[a][rp][i], pack2f(rf[i], rf[i]), acc);
       float t0, t1;
       unpack2f(acc, t0, t1);
 #pragma unroll
@@ -280,7 +268,7 @@ __global__ void __launch_bounds__(NT, MINB)
         Rp[i] = grid_split(Rd[i].hi, Rd[i].lo, C);
         Lf[i] = Ld[i].hi + Ld[i].lo;  // rounded to nearest (hi alone is truncated)
       }
-      rem_edge<M>(Lp, Rp, rho, xa);
+      rem_edge<M>(Lp, Rp, co.edge2, co.ts02, rho, xa);
       rem_add_rr0<M>(co.rr[0][0], rho, xa, rf);
 #pragma unroll
       for (int r = 0; r < M; ++r) {
@@ -289,7 +277,7 @@ __global__ void __launch_bounds__(NT, MINB)
         sX0[xd0[k] + r * XS] = df32{h, l};
       }
       float xg[NA > 1 ? NA - 1 : 1][M];
-      rem_grades<M, NA>(co.ts[0], co.rr[0], co.scale[0], Lf, rf, xg);
+      rem_grades<M, NA>(co.ts[0], co.rr[0], co.rr2[0], co.scale[0], Lf, rf, xg);
 #pragma unroll
       for (int a = 1; a < NA; ++a)
 #pragma unroll
@@ -328,10 +316,10 @@ __global__ void __launch_bounds__(NT, MINB)
         Rp[i] = grid_split(R0[i].hi, R0[i].lo, C);
         Lf[i] = L0[i].hi + L0[i].lo;
       }
-      rem_edge<M>(Lp, Rp, rho, ya);
+      rem_edge<M>(Lp, Rp, co.edge2, co.ts02, rho, ya);
       rem_add_rr0<M>(co.rr[1][0], rho, ya, rf);
       float yg[NA > 1 ? NA - 1 : 1][M];
-      rem_grades<M, NA>(co.ts[1], co.rr[1], co.scale[1], Lf, rf, yg);
+      rem_grades<M, NA>(co.ts[1], co.rr[1], co.rr2[1], co.scale[1], Lf, rf, yg);
       H *y0o = sY0 + (p & 1) * Sh::SY0 + yd0[k];
       float *y1o = sY1 + (p & 1) * Sh::SY1 + yd1[k];
 #pragma unroll
@@ -402,10 +390,10 @@ __global__ void __launch_bounds__(NT, MINB)
             Rp[i] = grid_split(R0[i].hi, R0[i].lo, C);
             Lf[i] = L0[i].hi + L0[i].lo;
           }
-          rem_edge<M>(Lp, Rp, rho, z0p[fi]);
+          rem_edge<M>(Lp, Rp, co.edge2, co.ts02, rho, z0p[fi]);
           rem_add_rr0<M>(co.rr[2][0], rho, z0p[fi], rf);
           float zg[NA > 1 ? NA - 1 : 1][M];
-          rem_grades<M, NA>(co.ts[2], co.rr[2], co.scale[2], Lf, rf, zg);
+          rem_grades<M, NA>(co.ts[2], co.rr[2], co.rr2[2], co.scale[2], Lf, rf, zg);
 #pragma unroll
           for (int r = 0; r < M; ++r) {
             float h, l;

@@ -275,6 +275,19 @@ void build_rem_coeffs(int m, const double h[3], double c, double tau, const Step
           for (int g = 1; g < 3; ++g)
             out->kz2[fo][fi][g - 1][rp][i] =
                 pair(out->kz[fo][fi][g][2 * rp * 4 + i], out->kz[fo][fi][g][(2 * rp + 1) * 4 + i]);
+      for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 3; ++a) out->rr2[d][a][rp][i] = pair(out->rr[d][a][2 * rp][i], out->rr[d][a][2 * rp + 1][i]);
+    }
+  // the remainder rho_i = R_i - sum_{j>=i} C(j, i) L_j and the Taylor shift to the
+  // cell centre, sum_{j>r} C(j, r) 2^-(j-r) L_j (the coefficient of xi^r of (xi + 1/2)^j)
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      long long bc = 1;  // C(j, i)
+      for (int k = 1; k <= i; ++k) bc = bc * (j - i + k) / k;
+      const float nb = j >= i ? -(float)bc : 0.f;
+      const float ts = j > i ? (float)bc / (float)(1 << (j - i)) : 0.f;
+      out->edge2[i][j] = pair(nb, nb);
+      out->ts02[i][j] = pair(ts, ts);
     }
 }
 
