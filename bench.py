@@ -543,7 +543,8 @@ def run_advection(torch, rank, world, max_over_ranks, hbm_peak, side=150, nsteps
 def run_batch(torch, rank, nhalf=200):
     """The batched workload: 64 seeded simulations (sides from {32,48,64,96}
     per dimension, m from {1,2,3}, Gaussian pulses), FP32, 200 half steps as
-    one CUDA graph of persistent launches, z-chunks from the autotuner."""
+    one CUDA graph of persistent launches, tile shapes and z-chunks per order
+    from the autotuner."""
     import hermite_inputs as HI
     from paper_1609_09841_gb300.autotune import tune_batch
     from paper_1609_09841_gb300.batch import BatchPlan
@@ -564,7 +565,7 @@ def run_batch(torch, rank, nhalf=200):
     ms = e0.elapsed_time(e1)
     dofs = sum(bp.dof(i) for i in range(len(sims)))
     return {"value": dofs * nhalf / (ms * 1e-3), "unit": "DOF-updates/s", "sims": len(sims), "half_steps": nhalf,
-            "ms_total": ms, "zchunk": tuned["zchunk"], "launches": nhalf}
+            "ms_total": ms, "tile": tuned["tile"], "zchunk": tuned["zchunk"], "launches": nhalf}
 
 
 def run_reference(args):

@@ -71,8 +71,10 @@ def tune(plan, x, y, zchunks=ZCHUNKS, reps=2, cache=DEFAULT_CACHE, force=False):
     return best
 
 
-BATCH_ZCHUNKS = (8, 16, 32, 64)
+BATCH_ZCHUNKS = (8, 16, 32, 48, 64, 96)
 BATCH_TILES = (0, 1)
+# whole z-chunk triples (orders 1, 2, 3) timed first; the search starts from the fastest
+BATCH_STARTS = ((8, 8, 8), (16, 16, 16), (32, 16, 8), (32, 32, 16), (64, 32, 16), (96, 48, 32))
 
 
 def _time_batch(bplan, a, b, reps):
@@ -91,21 +93,26 @@ def _time_batch(bplan, a, b, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, reps=3, sweeps=2):
+def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, starts=BATCH_STARTS, reps=3, sweeps=2):
     """Pick and apply the fastest tile shape x z-chunk of every order present
     in a batched plan.  The orders share one persistent launch, so they are
-    tuned by coordinate search: for each order in turn (heaviest first) every
-    (tile, zchunk) pair is timed with the other orders held at their current
-    choice, and the fastest is kept; `sweeps` passes over the orders.  Timing:
+    tuned by coordinate search: from the fastest of the whole z-chunk triples
+    `starts` (first tile shapes), each order in turn (heaviest first) has every
+    (tile, zchunk) pair timed with the other orders held at their current
+    choice, and keeps the fastest; `sweeps` passes over the orders.  Timing:
     `reps` batched half steps after a warm-up one (CUDA events).  Returns
     {"tile", "zchunk" (per order 1..3), "ms", "table" (every timing)}."""
     orders = sorted({s["m"] for s in bplan.sims}, reverse=True)
-    tile, zc = [0, 0, 0], [16, 16, 16]
+    tile = [0, 0, 0]
     bplan.set_tiles(tile)
-    bplan.set_schedule(zc)
     table = {}
-    best_ms = _time_batch(bplan, a, b, reps)
-    table[f"start {tile} {zc}"] = best_ms
+    best_ms, zc = None, None
+    for z3 in starts:
+        bplan.set_schedule(z3)
+        ms = _time_batch(bplan, a, b, reps)
+        table[f"start {list(z3)}"] = ms
+        if best_ms is None or ms < best_ms:
+            best_ms, zc = ms, list(z3)
     for sweep in range(sweeps):
         for m in orders:
             choice = (tile[m - 1], zc[m - 1])

@@ -109,16 +109,8 @@ static_assert(shape_smem<float, 2, 1>() <= shape_smem<float, 3, 0>() &&
                   shape_smem<float, 4, 1>() <= shape_smem<float, 3, 0>(),
               "the second shapes must not raise the batched kernel's shared memory");
 
-// Each (order, shape) body is its own function: inlined into one kernel the
-// six bodies share one register allocation and spill inside the tile loops.
-#ifdef HERMITE_BATCH_INLINE
-#define HERMITE_BATCH_TILE_FN __forceinline__
-#else
-#define HERMITE_BATCH_TILE_FN __noinline__
-#endif
-
 template <typename TS, typename TC, int M, int K>
-__device__ HERMITE_BATCH_TILE_FN void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
+__device__ __forceinline__ void batch_tile(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
                                            const PackedCoeffs *pc, TC *sX, int s) {
   constexpr int TX = BatchTile<M, K>::TX, TY = BatchTile<M, K>::TY;
   using Sh = FusedShape<TC, M, TX, TY>;
@@ -136,7 +128,20 @@ __device__ HERMITE_BATCH_TILE_FN void batch_tile(const BatchSim &sm, const Batch
       (const TS *)sm.in, (TS *)sm.out, g, x0, y0, z0, z1, co, sX, sX + Sh::SX, pc);
 }
 
-template <typename TS, typename TC>
+// The generic kernel calls each (order, shape) body as its own function:
+// inlined into one kernel, six bodies share one register allocation and spill
+// in the tile loops (892 B); the first-shape kernel inlines its three.
+template <typename TS, typename TC, int M, int K>
+__device__ __noinline__ void batch_tile_fn(const BatchSim &sm, const BatchItem &it, const StepCoeffs<TC> &co,
+                                           const PackedCoeffs *pc, TC *sX, int s) {
+  batch_tile<TS, TC, M, K>(sm, it, co, pc, sX, s);
+}
+
+// GENERIC = false: every order on its first tile shape (three inlined bodies;
+// measured 7.00 ms per half step on the 64-simulation workload against 7.83 ms
+// for the generic kernel with the same shapes).  GENERIC = true: any shape per
+// order.
+template <typename TS, typename TC, bool GENERIC>
 __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
     batch_step_kernel(const BatchSim *__restrict__ sims, const unsigned char *__restrict__ coeffs,
                       const BatchItem *__restrict__ items, int nitems, int *__restrict__ counter, int s) {
@@ -160,31 +165,39 @@ __global__ void __launch_bounds__(kBatchThreads, HERMITE_BATCH_MIN_BLOCKS)
       for (int k = threadIdx.x; k < (int)(batch_record_bytes<TC>() / 8); k += kBatchThreads) dst[k] = src[k];
     }
     __syncthreads();
-    switch (sm.m * kBatchShapes + sm.shape) {
-      case 1 * kBatchShapes + 0: batch_tile<TS, TC, 2, 0>(sm, it, *sco, spc, sX, s); break;
-      case 1 * kBatchShapes + 1: batch_tile<TS, TC, 2, 1>(sm, it, *sco, spc, sX, s); break;
-      case 2 * kBatchShapes + 0: batch_tile<TS, TC, 3, 0>(sm, it, *sco, spc, sX, s); break;
-      case 2 * kBatchShapes + 1: batch_tile<TS, TC, 3, 1>(sm, it, *sco, spc, sX, s); break;
-      case 3 * kBatchShapes + 0: batch_tile<TS, TC, 4, 0>(sm, it, *sco, spc, sX, s); break;
-      case 3 * kBatchShapes + 1: batch_tile<TS, TC, 4, 1>(sm, it, *sco, spc, sX, s); break;
-      default: break;  // the host builds only the pairs above
+    if constexpr (GENERIC) {
+      switch (sm.m * kBatchShapes + sm.shape) {
+        case 1 * kBatchShapes + 0: batch_tile_fn<TS, TC, 2, 0>(sm, it, *sco, spc, sX, s); break;
+        case 1 * kBatchShapes + 1: batch_tile_fn<TS, TC, 2, 1>(sm, it, *sco, spc, sX, s); break;
+        case 2 * kBatchShapes + 0: batch_tile_fn<TS, TC, 3, 0>(sm, it, *sco, spc, sX, s); break;
+        case 2 * kBatchShapes + 1: batch_tile_fn<TS, TC, 3, 1>(sm, it, *sco, spc, sX, s); break;
+        case 3 * kBatchShapes + 0: batch_tile_fn<TS, TC, 4, 0>(sm, it, *sco, spc, sX, s); break;
+        case 3 * kBatchShapes + 1: batch_tile_fn<TS, TC, 4, 1>(sm, it, *sco, spc, sX, s); break;
+        default: break;  // the host builds only the pairs above
+      }
+    } else {
+      switch (sm.m) {
+        case 1: batch_tile<TS, TC, 2, 0>(sm, it, *sco, spc, sX, s); break;
+        case 2: batch_tile<TS, TC, 3, 0>(sm, it, *sco, spc, sX, s); break;
+        default: batch_tile<TS, TC, 4, 0>(sm, it, *sco, spc, sX, s); break;
+      }
     }
     __syncthreads();  // every thread is done with sco, sX, sY and s_item
   }
 }
 
-template <typename TS, typename TC>
+template <typename TS, typename TC, bool GENERIC>
 static SmemAttrOnce &batch_smem_once() {  // dynamic shared-memory limit raised, per device
   static SmemAttrOnce once;
   return once;
 }
 
-template <typename TS, typename TC>
+template <typename TS, typename TC, bool GENERIC>
 static cudaError_t launch_batch_t(const BatchSim *sims, const void *coeffs, const BatchItem *items, int nitems,
                                   int *counter, int s, int grid, cudaStream_t st) {
-  auto kern = batch_step_kernel<TS, TC>;
+  auto kern = batch_step_kernel<TS, TC, GENERIC>;
   constexpr size_t smem = batch_smem_bytes<TC>() + 16;
-  cudaError_t e = raise_smem_limit(batch_smem_once<TS, TC>(), kern, smem);
+  cudaError_t e = raise_smem_limit(batch_smem_once<TS, TC, GENERIC>(), kern, smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -192,12 +205,12 @@ static cudaError_t launch_batch_t(const BatchSim *sims, const void *coeffs, cons
   return cudaGetLastError();
 }
 
-template <typename TS, typename TC>
+template <typename TS, typename TC, bool GENERIC>
 static int occupancy_t() {
   int blocks = 0;
   constexpr size_t smem = batch_smem_bytes<TC>() + 16;
-  auto kern = batch_step_kernel<TS, TC>;
-  if (raise_smem_limit(batch_smem_once<TS, TC>(), kern, smem) != cudaSuccess) cudaGetLastError();
+  auto kern = batch_step_kernel<TS, TC, GENERIC>;
+  if (raise_smem_limit(batch_smem_once<TS, TC, GENERIC>(), kern, smem) != cudaSuccess) cudaGetLastError();
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kBatchThreads, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -205,16 +218,31 @@ static int occupancy_t() {
   return blocks > 0 ? blocks : 1;
 }
 
-int batch_blocks_per_sm(int compute, int state) {
-  if (compute == kF64) return occupancy_t<double, double>();
-  return state == kF64 ? occupancy_t<double, float>() : occupancy_t<float, float>();
+template <typename TS, typename TC>
+static int occupancy_both() {  // both kernels take the same persistent grid
+  const int a = occupancy_t<TS, TC, false>(), b = occupancy_t<TS, TC, true>();
+  return a < b ? a : b;
 }
 
-cudaError_t launch_batch(int compute, int state, const BatchSim *sims, const void *coeffs, const BatchItem *items,
-                         int nitems, int *counter, int s, int grid, cudaStream_t st) {
-  if (compute == kF64) return launch_batch_t<double, double>(sims, coeffs, items, nitems, counter, s, grid, st);
-  if (state == kF64) return launch_batch_t<double, float>(sims, coeffs, items, nitems, counter, s, grid, st);
-  return launch_batch_t<float, float>(sims, coeffs, items, nitems, counter, s, grid, st);
+int batch_blocks_per_sm(int compute, int state) {
+  if (compute == kF64) return occupancy_both<double, double>();
+  return state == kF64 ? occupancy_both<double, float>() : occupancy_both<float, float>();
+}
+
+template <bool GENERIC>
+static cudaError_t launch_batch_g(int compute, int state, const BatchSim *sims, const void *coeffs,
+                                  const BatchItem *items, int nitems, int *counter, int s, int grid,
+                                  cudaStream_t st) {
+  if (compute == kF64)
+    return launch_batch_t<double, double, GENERIC>(sims, coeffs, items, nitems, counter, s, grid, st);
+  if (state == kF64) return launch_batch_t<double, float, GENERIC>(sims, coeffs, items, nitems, counter, s, grid, st);
+  return launch_batch_t<float, float, GENERIC>(sims, coeffs, items, nitems, counter, s, grid, st);
+}
+
+cudaError_t launch_batch(int compute, int state, bool generic, const BatchSim *sims, const void *coeffs,
+                         const BatchItem *items, int nitems, int *counter, int s, int grid, cudaStream_t st) {
+  return generic ? launch_batch_g<true>(compute, state, sims, coeffs, items, nitems, counter, s, grid, st)
+                 : launch_batch_g<false>(compute, state, sims, coeffs, items, nitems, counter, s, grid, st);
 }
 
 }  // namespace hermite

@@ -30,7 +30,9 @@ void batch_tile_shape(int m, int shape, int *tx, int *ty);
 size_t batch_coeff_record_bytes(int compute);
 void batch_write_record(int compute, const StepCoeffs<double> &cd, unsigned char *dst);
 int batch_blocks_per_sm(int compute, int state);
-cudaError_t launch_batch(int compute, int state, const BatchSim *sims, const void *coeffs, const BatchItem *items,
-                         int nitems, int *counter, int s, int grid, cudaStream_t st);
+// generic = false: every order on tile shape 0 (the kernel with those bodies
+// inlined); true: the kernel that takes any shape per order.
+cudaError_t launch_batch(int compute, int state, bool generic, const BatchSim *sims, const void *coeffs,
+                         const BatchItem *items, int nitems, int *counter, int s, int grid, cudaStream_t st);
 
 }  // namespace hermite

@@ -137,7 +137,8 @@ int get_set(BatchPlan *b, const void *const *in, void *const *out, BatchSim **de
 }
 
 int launch(BatchPlan *b, BatchSim *d, int parity, cudaStream_t st) {
-  const cudaError_t e = launch_batch(b->compute, b->state == HERMITE_STATE_FP64 ? kF64 : kF32, d, b->coeffs,
+  const bool generic = b->shape[1] != 0 || b->shape[2] != 0 || b->shape[3] != 0;
+  const cudaError_t e = launch_batch(b->compute, b->state == HERMITE_STATE_FP64 ? kF64 : kF32, generic, d, b->coeffs,
                                      b->items, b->nitems, b->counter, parity == 0 ? 0 : -1, b->grid, st);
   return e == cudaSuccess ? HERMITE_OK : cuda_fail(e, "batched half-step launch");
 }
