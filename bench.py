@@ -60,9 +60,10 @@ VARIANTS = {
 # per cell, both fields, M = m + 1.  Reported as a nominal ALU figure only.
 FLOP_PER_NODE = {m: 2 * 30 * (m + 1) ** 4 + 28 * (m + 1) ** 3 for m in (1, 2, 3)}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (ncu captures at 128^3 scaled by the
-# node count x 8; profiles/), keyed by (variant, m, side).  None where no capture of the current
-# kernel exists.
-TRAFFIC_BYTES = {("fp32", 3, 256): 17.95e9}
+# node count x 8; profiles/), keyed by (variant, m, side, tile): the remainder form's tile 1
+# (8 x 2 cells) and FP32's staged tile 6, the schedules the autotuner picks at 256^3.  None where
+# no capture of the kernel the run timed exists.
+TRAFFIC_BYTES = {("remainder", 3, 256, 1): 35.49e9, ("fp32", 3, 256, 6): 22.53e9}
 
 
 def dof_per_step(m=M_ORDER, n=N_SIDE):
@@ -451,7 +452,7 @@ def run_ours(args, rank, world):
                      "t1_max_rel": hr["t1_max_rel"], "bar": BAR, "meets_bar": hr["meets_bar"],
                      "speedup_vs_fp64": hr.get("speedup_vs_fp64")},
         "roofline": {"bound": "hbm", "achieved": hr["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
-                     "frac": hr["hbm_frac"], "traffic": TRAFFIC_BYTES.get((head, m, args.side)),
+                     "frac": hr["hbm_frac"], "traffic": TRAFFIC_BYTES.get((head, m, args.side, hr["schedule"].get("tile"))),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                      "bytes_per_launch": hr["bytes_per_step"],
                      "bytes_rule": f"one state read + one written: 2 x 2(m+1)^3 x {8 if state == 'fp64' else 4} B "
