@@ -174,7 +174,7 @@ def cpu_baseline(max_seconds=30.0):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms while running."""
 
     def __init__(self):
         self.proc, self.path = None, None
@@ -187,7 +187,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(int(os.environ.get("LOCAL_RANK", 0)))],
+                                          "-lms", "50", "-i", str(int(os.environ.get("LOCAL_RANK", 0)))],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
