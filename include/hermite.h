@@ -204,6 +204,16 @@ int hermite_debug_status(hermite_plan_t plan, int *flags, unsigned long long *fi
 int hermite_debug_selftest(hermite_plan_t plan, const void *in, void *out, int parity, double fraction,
                            void *stream);
 
+/* Debug builds only (EUNSUPPORTED in release builds): one forward half step
+ * as a drill of the kernels' bounded waits.  The awaited work is never issued
+ * (no plane copy of a staged FP32 schedule, tiles 6 and 7; no MMA of a
+ * tensor-core precision) and every wait gives up after a few polls, so each
+ * CTA that would wait takes its failure path: it sets bit 0 of the status
+ * word (hermite_device_status), waits once more (bounded), releases what it
+ * holds and leaves its tile.  `out` is then incomplete.  EINVAL for other
+ * plans or schedules and for the buffer rules of hermite_step. */
+int hermite_debug_wait_drill(hermite_plan_t plan, const void *in, void *out, int parity, void *stream);
+
 /* Device status of the plan's kernels: *status receives the OR of the flags
  * that kernels raised since the last call (0: none) and the flags are
  * cleared.  Bit 0: a CTA gave up after a bounded wait, its outputs then

@@ -91,6 +91,7 @@ def load_library(path=LIB_PATH):
         "hermite_debug_build": (I, []),
         "hermite_debug_status": (I, [P, IP, ctypes.POINTER(ctypes.c_ulonglong), P]),
         "hermite_debug_selftest": (I, [P, P, P, I, D, P]),
+        "hermite_debug_wait_drill": (I, [P, P, P, I, P]),
         "hermite_record": (I, [P, P, P, I, P, P]),
         "hermite_inject": (I, [P, P, P, I, P, P]),
         "hermite_last_error": (ctypes.c_char_p, []),

@@ -112,6 +112,7 @@ Geom geom_of(const hermite_plan_s *p, int s) {
   g.zhi = g.nz;
   g.elems = p->dbg_bound ? p->dbg_bound : p->elems;
   g.dbg = p->dbg;
+  g.drill = p->drill;
   return g;
 }
 
@@ -734,6 +735,20 @@ int hermite_debug_selftest(hermite_plan_t p, const void *in, void *out, int pari
   if (p->dbg_bound == 0) p->dbg_bound = 1;
   const int rc = run_step(p, in, out, parity, kForward, (cudaStream_t)stream);
   p->dbg_bound = 0;
+  return rc;
+}
+
+int hermite_debug_wait_drill(hermite_plan_t p, const void *in, void *out, int parity, void *stream) {
+  if (!kDebugBuild) return fail(HERMITE_EUNSUPPORTED, "not a debug build");
+  if (!p || p->batch || p->eq) return fail(HERMITE_EINVAL, "plan is NULL, batched or advection");
+  const bool staged = p->prec == HERMITE_FP32 && p->q == 4 && p->variant != HERMITE_SPLIT && p->tile >= kFirstStagedTile;
+  if (!staged && !is_tc_prec(p->prec))
+    return fail(HERMITE_EINVAL, "the drill needs a tensor-core precision or a staged FP32 schedule");
+  if (parity != 0 && parity != 1) return fail(HERMITE_EINVAL, "parity %d not 0 or 1", parity);
+  if (int rc = check_device_only(p, in, out, "hermite_debug_wait_drill")) return rc;
+  p->drill = 1;
+  const int rc = run_step(p, in, out, parity, kForward, (cudaStream_t)stream);
+  p->drill = 0;
   return rc;
 }
 

@@ -221,6 +221,9 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   const int xa = xs0 >= 0 ? xs0 / Sg::U * Sg::U : -((-xs0 + Sg::U - 1) / Sg::U) * Sg::U;
   bool use_tma = false;
   if constexpr (ST) use_tma = stg->map_ok && xa >= 0 && xa + Sg::BW <= nx && y0 + s >= 0 && y0 + s + TY < ny;
+  // debug-build drill: no copy is issued, so every wait of a copied tile runs out
+  const bool drill = kDebugBuild && g.drill != 0;
+  const uint32_t polls = drill ? kDrillPolls : kStageMaxPolls;
 
   // x-items: source planes and in-plane offsets of the edge's two nodes
   // (staged: xl is the left node's place in the window, xr unused).
@@ -265,6 +268,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
   // one thread starts the copy of plane pp's window into buffer pp % NB
   auto stage_issue = [&](int pp) {
     if constexpr (ST) {
+      if (drill) return;
       uint64_t *mb = stg->mbar + pp % NB;
       tc::fence_async_smem();  // the x-pass's reads of the buffer come before the copy's writes
       tma::arrive_expect_tx(mb, (uint32_t)(Sg::ELEMS * sizeof(TS)));
@@ -322,7 +326,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
     if constexpr (ST) {
       TS *bp = stg->buf + (p % NB) * Sg::STRIDE;
       if (use_tma) {
-        stage_failed = !tc::mbar_wait(stg->mbar + p % NB, (uint32_t)((p / NB) & 1), kStageMaxPolls);
+        stage_failed = !tc::mbar_wait(stg->mbar + p % NB, (uint32_t)((p / NB) & 1), polls);
       } else {
         for (int e = threadIdx.x; e < Sg::ELEMS; e += NT)
           bp[e] = state_load(g, in, in + (size_t)(e / Sg::BCS) * plane + zoff + stg->tab[e % Sg::BCS]);
@@ -401,7 +405,7 @@ __device__ __forceinline__ void fused_tile(const TS *__restrict__ in, TS *__rest
           atomicOr(stg->status, 1);
           // copies may still land: one more bounded wait on each before the shared memory is released
           for (int q = p; q < p + NB && q <= z1 - z0; ++q)
-            tc::mbar_wait(stg->mbar + q % NB, (uint32_t)((q / NB) & 1), kStageMaxPolls);
+            tc::mbar_wait(stg->mbar + q % NB, (uint32_t)((q / NB) & 1), polls);
         }
         __syncthreads();
         return;
@@ -687,8 +691,10 @@ cudaError_t launch_fused_st_cfg(const TS *in, TS *out, const Geom &g, const Step
   if constexpr (std::is_same<TC, float>::value) pc = pack_coeffs(co);
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
-  const int map_ok = !kDebugBuild && encode_state_map(&map, in, (int)sizeof(TS), g.nx, g.ny, g.nz, Sg::NC, Sg::BW,
-                                                      Sg::ROWS);
+  // debug builds: plain loads (every read bounds-checked), except in a wait drill, where the map
+  // is encoded so that the copied tiles wait (for copies that are never issued)
+  const int map_ok = (!kDebugBuild || g.drill) &&
+                     encode_state_map(&map, in, (int)sizeof(TS), g.nx, g.ny, g.nz, Sg::NC, Sg::BW, Sg::ROWS);
   kern<<<grid, NT, smem, st>>>(in, out, g, zchunk, co, pc, map, map_ok, status);
   return cudaGetLastError();
 }

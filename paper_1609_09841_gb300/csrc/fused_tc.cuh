@@ -334,6 +334,9 @@ __global__ void __launch_bounds__(NT, 2)
   const int np = z1 - z0 + 1;
   bool failed = false;
   uint32_t failed_phase = 0;
+  // debug-build drill: no MMA is issued, so every wait runs out and takes the failure path
+  const bool drill = kDebugBuild && g.drill != 0;
+  const uint32_t polls = drill ? kDrillPolls : kTcMaxPolls;
   xpass(0);
   __syncthreads();
   for (int p = 0; p < np; ++p) {
@@ -342,10 +345,10 @@ __global__ void __launch_bounds__(NT, 2)
     __syncthreads();
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
-      issue_mma();
+      if (!drill) issue_mma();
     }
     if (p + 1 < np) xpass(p + 1);  // overlaps the MMAs (they read A and B only)
-    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&mbar, (uint32_t)(p & 1), kTcMaxPolls));
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&mbar, (uint32_t)(p & 1), polls));
     tc::fence_after_sync();
     if (ok && warp_has_rows) {
       float v[16];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(NT, 2)
     if (threadIdx.x == 0) atomicOr(status, 1);
     // give the MMAs in flight one more bounded chance to finish before the
     // tensor memory they write is released
-    tc::mbar_wait(&mbar, failed_phase, kTcMaxPolls);
+    tc::mbar_wait(&mbar, failed_phase, polls);
     __syncthreads();
   }
   if (threadIdx.x < 32) tc::tmem_dealloc(tmem, T::TMEM_COLS);

@@ -124,7 +124,12 @@ struct Geom {
   int zlo, zhi;  // output z layers [zlo, zhi) computed by a launch (the fused and hybrid kernels)
   size_t elems = 0;             // elements of one state (debug build: the bound of every index; 0: unchecked)
   DebugRecord *dbg = nullptr;   // debug build: where out-of-range accesses are recorded
+  int drill = 0;                // debug build: bounded-wait drill (hermite_debug_wait_drill)
 };
+
+// Polls of a bounded wait in a drill step: the awaited copy or MMA is never
+// issued, so every wait runs out after these polls and takes its failure path.
+constexpr unsigned kDrillPolls = 64;
 
 // Bounds checks of the debug build (compiled with -DHERMITE_DEBUG): the
 // fused kernels route every global load and store of a state through these;

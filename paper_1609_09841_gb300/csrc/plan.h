@@ -34,6 +34,7 @@ struct hermite_plan_s {
   int *status = nullptr;                    // device status word of the tensor-core kernel
   hermite::DebugRecord *dbg = nullptr;      // debug build: record of the kernels' bounds checks
   size_t dbg_bound = 0;                     // debug self-test: bound handed to the kernels (0: elems)
+  int drill = 0;                            // debug build: the next step is a bounded-wait drill
   hermite::InterpCoeffs<double> interp;
   hermite::EvolveParams evolve;
   int q = 4;                // Taylor stages of the local evolution (4 = RK4)

@@ -6,7 +6,11 @@
 * hermite_debug_selftest tells the kernels that the state holds half its
   elements: the loads and stores past that are flagged (bits 1 and 2) with
   the first offending offset at the half, and skipped -- on full-size
-  buffers, so no access could leave them in any case."""
+  buffers, so no access could leave them in any case.
+* hermite_debug_wait_drill runs a half step whose awaited work (the plane
+  copies of a staged FP32 schedule, the MMAs of the tensor-core kernel) is
+  never issued: every bounded wait runs out, the status bit is set, and the
+  next ordinary step gives the same bits as before the drill."""
 import ctypes
 
 import numpy as np
@@ -88,4 +92,41 @@ def test_debug_selftest_flags_and_skips_accesses_past_the_bound(libs, name):
     flat = y.flatten().cpu().numpy()
     assert np.all(flat[elems // 2:] == 7.0)        # stores past the bound were skipped
     assert _status(dbg, p) == (0, 2 ** 64 - 1)     # cleared by the read
+    dbg.hermite_destroy(p)
+
+
+@pytest.mark.parametrize("name,m,n,tile", [("fp32", 3, (24, 12, 8), 6), ("fp32", 2, (24, 12, 8), 7),
+                                           ("3xtf32", 3, (16, 12, 8), 0)])
+def test_wait_drill_sets_status_and_leaves_the_context_usable(libs, name, m, n, tile):
+    """The drill's waits give up after a few polls and set bit 0 of the status
+    word; nothing is left waiting, and the plan and the context keep working."""
+    torch, capi, dbg = libs
+    prec, state = PRECS[name]
+    p = _plan(dbg, m, n, prec, state)
+    assert dbg.hermite_set_schedule(p, tile, 4) == 0
+    x = HI.random_state(m, n, seed=12)
+    xd = torch.from_numpy(x).to(torch.float32).cuda()
+    xp, yp = ctypes.c_void_p(xd.data_ptr()), None
+    before = torch.empty_like(xd)
+    assert dbg.hermite_step(p, xp, ctypes.c_void_p(before.data_ptr()), 0, None) == 0
+    st = ctypes.c_int()
+    assert dbg.hermite_device_status(p, ctypes.byref(st), None) == 0 and st.value == 0
+    y = torch.empty_like(xd)
+    yp = ctypes.c_void_p(y.data_ptr())
+    assert dbg.hermite_debug_wait_drill(p, xp, yp, 0, None) == 0
+    assert dbg.hermite_device_status(p, ctypes.byref(st), None) == 0 and st.value == 1
+    after = torch.full_like(xd, float("nan"))
+    assert dbg.hermite_step(p, xp, ctypes.c_void_p(after.data_ptr()), 0, None) == 0
+    assert dbg.hermite_device_status(p, ctypes.byref(st), None) == 0 and st.value == 0
+    assert torch.equal(before, after)
+    dbg.hermite_destroy(p)
+
+
+def test_wait_drill_rejects_plans_without_bounded_waits(libs):
+    torch, capi, dbg = libs
+    p = _plan(dbg, 2, (8, 8, 8), 1, 1)     # FP32, default tile 0: plain loads, no waits
+    x = torch.zeros(2 * 27 * 512, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    rc = dbg.hermite_debug_wait_drill(p, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), 0, None)
+    assert rc == capi.HERMITE_EINVAL
     dbg.hermite_destroy(p)
