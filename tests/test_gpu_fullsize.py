@@ -76,12 +76,14 @@ def test_config2_size_fp64_sampled(torch_cuda, variant):
     _sampled_parity(torch, plan, m, n, h, 1.0, dt, torch.float64, 1e-12)
 
 
-@pytest.mark.parametrize("state,schedule", [("fp32", None), ("fp64", None), ("fp32", (5, 64)), ("fp64", (5, 64))])
+@pytest.mark.parametrize("state,schedule", [("fp32", None), ("fp64", None), ("fp32", (5, 64)), ("fp64", (5, 64)),
+                                            ("fp32", (6, 32)), ("fp64", (6, 32))])
 def test_metric_size_fp32_sampled(torch_cuda, state, schedule):
     """m = 3, 256^3 (the throughput workload) with FP32 arithmetic; the sample
     is compared with the FP64 oracle on the same (rounded) input.  Schedule
-    (5, 64) is the 8x2-cell, 256-thread tile with z-chunk 64 that the bench's
-    autotuner picks and times at this size."""
+    (5, 64) is the best plain-load tile (8x2 cells, 256 threads, z-chunk 64);
+    (6, 32) the staged tile with z-chunk 32 that the bench's autotuner picks
+    and times at this size."""
     torch = torch_cuda
     from paper_1609_09841_gb300 import Plan
     m, n = 3, (256, 256, 256)
@@ -91,3 +93,59 @@ def test_metric_size_fp32_sampled(torch_cuda, state, schedule):
     if schedule is not None:
         plan.set_schedule(*schedule)
     _sampled_parity(torch, plan, m, n, h, 1.0, dt, torch.float32 if state == "fp32" else torch.float64, 2e-5)
+
+
+@pytest.mark.parametrize("schedule", [None, (1, 64)])
+def test_metric_size_remainder_sampled(torch_cuda, schedule):
+    """The headline variant at its full size: remainder form, FP64 state,
+    m = 3, 256^3, in the launch configuration the bench times (tile 1, 8x2
+    cells, z-chunk 64).  Seeded random data carries no smoothness, so the
+    remainders are as large as the data and the FP32 parts set the error: the
+    FP32 bar, 2e-5 relative over the sample."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import Plan
+    m, n = 3, (256, 256, 256)
+    h = (1 / 256,) * 3
+    dt = 0.4 * h[0]
+    plan = Plan(m, n, h, 1.0, dt, prec="remainder", state="fp64")
+    if schedule is not None:
+        plan.set_schedule(*schedule)
+    _sampled_parity(torch, plan, m, n, h, 1.0, dt, torch.float64, 2e-5)
+
+
+def test_remainder_resolved_data_sampled(torch_cuda):
+    """Smooth data: the seeded standing modes of the plain-method FP64
+    workload (m = 3, 128^3, modes k in {1..6}^3), one half step of each
+    parity in the bench's launch configuration, sampled against the oracle.
+
+    The remainder form's FP32 parts act on the one-sided Taylor remainder
+    rho, about (kh)^(m+1)/(m+1)! of the data, through factors with row sums
+    up to 3e4 (m = 3, grade 2), so its per-step error is about
+    eps32 * 3e4 * (kh)^4/4! relative.  The largest mode here has
+    kh = 2 pi 6 sqrt(3) / 128 = 0.51: 2^-24 * 3e4 * 2.8e-3 = 5e-6 (measured
+    3.5e-6).  On the precision workload (a Gaussian with sigma = 0.05, kh of
+    0.08-0.16 at 128^3) the same estimate is below 1e-8 per step."""
+    torch = torch_cuda
+    import hermite_inputs as HI
+    from paper_1609_09841_gb300 import Plan
+    m, n = 3, (128, 128, 128)
+    h = (1 / 128,) * 3
+    dt = 0.4 * h[0]
+    plan = Plan(m, n, h, 1.0, dt, prec="remainder", state="fp64")
+    plan.set_schedule(1, 64)
+    x = torch.from_numpy(HI.standing_modes(m, n, h, seed=1609)).cuda()
+    y = torch.empty_like(x)
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for parity in (0, 1):
+        plan.step(x, y, parity)
+        torch.cuda.synchronize()
+        nodes = np.stack([rng.integers(0, n[2], 96), rng.integers(0, n[1], 96), rng.integers(0, n[0], 96)], axis=1)
+        nodes[:2] = [[0, 0, 0], [n[2] - 1, n[1] - 1, n[0] - 1]]
+        U = _gather_corners(x, m, nodes, parity)
+        ref = oracle.cell_map(U, m, h, 1.0, dt / 2)
+        got = y[:, :, :, :, torch.as_tensor(nodes[:, 0], device="cuda"), torch.as_tensor(nodes[:, 1], device="cuda"),
+                torch.as_tensor(nodes[:, 2], device="cuda")].double().cpu().numpy().transpose(4, 0, 1, 2, 3)
+        worst = max(worst, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+    print({"remainder_smooth_data_per_step_max_rel": worst})
+    assert worst <= 1e-5
