@@ -75,18 +75,18 @@ enum hermite_status {
 enum hermite_prec {
   HERMITE_FP64 = 0,     /* FP64 throughout (state must be FP64) */
   HERMITE_FP32 = 1,     /* FP32 contractions, state FP32 or FP64 (loaded, computed in FP32, stored) */
-  HERMITE_HYBRID64 = 2, /* FP64 state; every contraction applied to grade-0 data (the node data,
-                           the x- and y-interpolants) in FP64, the rest (small grade >= 1 terms of
-                           the Taylor series) in FP32.  Fused variant only. */
-  HERMITE_HYBRIDDF = 3, /* as HYBRID64 with the FP64 part in double-float (pairs of FP32) */
   /* FP32 x- and y-passes; the z-pass (the mode product along x3 of the 1-D
      evolution-and-truncation factors, Sec. 3.1 Alg. 1/2 with Sec. 3.2's
      evolution folded in) on the tensor cores (tcgen05) with FP32 accumulation,
      its operands split into pieces of the tensor-core input type.  State FP32
      or FP64 (loaded, computed, stored back).  Fused variant, RK4 (q = 4),
      single-grid plans only. */
-  HERMITE_3XTF32 = 4,   /* y = a1 + a2 (TF32 pieces); a1 b1 + a1 b2 + a2 b1 */
-  HERMITE_SPLITBF16 = 5, /* y = a1 + a2 + a3 (BF16 pieces); the six products of total order <= 2 */
+  HERMITE_3XTF32 = 2,   /* y = a1 + a2 (TF32 pieces); a1 b1 + a1 b2 + a2 b1 */
+  HERMITE_SPLITBF16 = 3, /* y = a1 + a2 + a3 (BF16 pieces); the six products of total order <= 2 */
+  HERMITE_HYBRID64 = 4, /* FP64 state; every contraction applied to grade-0 data (the node data,
+                           the x- and y-interpolants) in FP64, the rest (small grade >= 1 terms of
+                           the Taylor series) in FP32.  Fused variant only. */
+  HERMITE_HYBRIDDF = 5, /* as HYBRID64 with the FP64 part in double-float (pairs of FP32) */
   /* FP64 state; every 1-D factor applied in the one-sided Taylor-remainder
      form G_a [L; R] = TS_a L + RR_a (R - T L), which Hermite interpolation's
      exactness on polynomials of degree <= 2m+1 (Sec. 3.1) allows: T L is the

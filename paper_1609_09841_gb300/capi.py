@@ -22,10 +22,10 @@ HERMITE_ENOCONV = -8
 
 HERMITE_FP64 = 0
 HERMITE_FP32 = 1
-HERMITE_HYBRID64 = 2
-HERMITE_HYBRIDDF = 3
-HERMITE_3XTF32 = 4
-HERMITE_SPLITBF16 = 5
+HERMITE_3XTF32 = 2
+HERMITE_SPLITBF16 = 3
+HERMITE_HYBRID64 = 4
+HERMITE_HYBRIDDF = 5
 HERMITE_REMAINDER = 6
 HERMITE_STATE_FP64 = 0
 HERMITE_STATE_FP32 = 1

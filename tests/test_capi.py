@@ -169,7 +169,7 @@ def test_taylor_order_validation(capi):
     assert capi.lib.hermite_set_taylor_order(p, 15) == 0
     assert capi.lib.hermite_taylor_order(p) == 15
     capi.lib.hermite_destroy(p)
-    rc, p = _plan(capi, m=2, prec=3, state=0)                        # double-float hybrid
+    rc, p = _plan(capi, m=2, prec=capi.HERMITE_HYBRIDDF, state=0)    # double-float hybrid
     assert rc == 0
     assert capi.lib.hermite_set_taylor_order(p, 6) == -4
     assert capi.lib.hermite_set_taylor_order(p, 4) == 0
@@ -219,5 +219,5 @@ def test_plan_taylor_checks_its_own_limit(capi):
     assert capi.lib.hermite_set_taylor_order(p, 5) == -5
     assert capi.lib.hermite_set_taylor_order(p, 21) == 0
     capi.lib.hermite_destroy(p)
-    assert _plan_q(capi, 2, 6, 2 * 0.2 * h, prec=2)[0] == -4   # hybrid: q = 4 only
+    assert _plan_q(capi, 2, 6, 2 * 0.2 * h, prec=capi.HERMITE_HYBRID64)[0] == -4   # hybrid: q = 4 only
     assert _plan_q(capi, 2, 2, 2 * 0.2 * h)[0] == -1

@@ -19,7 +19,7 @@ import pytest
 import hermite_inputs as HI
 
 pytestmark = pytest.mark.gpu
-PRECS = {"fp64": (0, 0), "fp32": (1, 1), "hybriddf": (3, 0), "3xtf32": (4, 1), "remainder": (6, 0)}
+PRECS = {"fp64": (0, 0), "fp32": (1, 1), "hybriddf": (5, 0), "3xtf32": (2, 1), "remainder": (6, 0)}
 
 
 @pytest.fixture(scope="module")
