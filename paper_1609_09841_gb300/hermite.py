@@ -128,8 +128,21 @@ class Plan:
             if _is_fp64(x) != (self.state == "fp64"):
                 raise ValueError(f"state dtype {x.dtype} does not match the plan's {self.state} state")
 
-    def step(self, x_in, x_out, parity, stream=None):
-        """x_out = S_parity(x_in) (device tensors: enqueued; host arrays: synchronous)."""
+    @staticmethod
+    def _out_and_parity(x_in, x_out, parity):
+        """(x_out, parity) of a call written f(x, y, parity) or f(x, parity),
+        the second allocating the output like x."""
+        if parity is None:
+            if not isinstance(x_out, (int, np.integer)):
+                raise TypeError("expected (x_in, x_out, parity) or (x_in, parity)")
+            parity = x_out
+            x_out = np.empty_like(x_in) if isinstance(x_in, np.ndarray) else x_in.new_empty(x_in.shape)
+        return x_out, parity
+
+    def step(self, x_in, x_out, parity=None, stream=None):
+        """x_out = S_parity(x_in) (device tensors: enqueued; host arrays: synchronous).
+        ``step(x, parity)`` allocates the output and returns it."""
+        x_out, parity = self._out_and_parity(x_in, x_out, parity)
         self._check(x_in, x_out)
         pi, di = _ptr(x_in)
         po, do = _ptr(x_out)
@@ -137,8 +150,10 @@ class Plan:
         capi.check(capi.lib.hermite_step(self.handle, ctypes.c_void_p(pi), ctypes.c_void_p(po), int(parity), st))
         return x_out
 
-    def adjoint(self, g_out, g_in, parity, stream=None):
-        """g_in = S_parity^T g_out (device tensors)."""
+    def adjoint(self, g_out, g_in, parity=None, stream=None):
+        """g_in = S_parity^T g_out (device tensors); ``adjoint(g, parity)``
+        allocates g_in and returns it."""
+        g_in, parity = self._out_and_parity(g_out, g_in, parity)
         self._check(g_out, g_in)
         capi.check(capi.lib.hermite_adjoint_step(self.handle, ctypes.c_void_p(_ptr(g_out)[0]),
                                                  ctypes.c_void_p(_ptr(g_in)[0]), int(parity), _stream(stream)))

@@ -124,3 +124,57 @@ def test_config5_gradient_fd_and_fp64(torch_cuda):
             assert abs(fd - ad) <= tol * max(abs(ad), 1e-30), (prec, fd, ad)
     a, b = grads["fp32"], grads["fp64"]
     assert float((a - b).norm() / b.norm()) <= 1e-4
+
+
+@pytest.mark.parametrize("every", [1, 4, 40])
+def test_hermite_run_matches_oracle(torch_cuda, every):
+    """HermiteRun (adjoint.run): the state after 11 half steps, the gradient
+    of L = <x_n, w> with respect to x0 (the oracle's adjoint sweep of w) and
+    dL/dc (central difference of the oracle's L in c), FP64, m = 2, on a
+    9 x 7 x 6 grid, checkpoints every 1, 4 (ragged last segment) or 40 half
+    steps."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import Plan
+    from paper_1609_09841_gb300.adjoint import run
+    m, n = 2, (9, 7, 6)
+    h = tuple(1.0 / v for v in n)
+    c, dt, nhalf = 1.1, 0.3 * min(h), 11
+    x0 = HI.random_state(m, n, seed=21)
+    w = HI.random_state(m, n, seed=22)
+    plan = Plan(m, n, h, c, dt)
+    xt = torch.from_numpy(x0).cuda().requires_grad_(True)
+    ct = torch.tensor(c, dtype=torch.float64, requires_grad=True)
+    y = run(plan, xt, nhalf, every, ct)
+    ((y * torch.from_numpy(w).cuda()).sum()).backward()
+
+    ref = oracle.run(x0, m, h, c, dt, nhalf)
+    assert np.max(np.abs(y.detach().cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    adj = w.copy()
+    for t in range(nhalf - 1, -1, -1):
+        adj = oracle.adjoint_half_step(adj, m, h, c, dt, t % 2)
+    g = xt.grad.cpu().numpy()
+    assert np.max(np.abs(g - adj)) <= 1e-12 * np.max(np.abs(adj))
+    dc = 1e-4
+    lp = float(np.sum(oracle.run(x0, m, h, c + dc, dt, nhalf) * w))
+    lm = float(np.sum(oracle.run(x0, m, h, c - dc, dt, nhalf) * w))
+    fd = (lp - lm) / (2 * dc)
+    assert abs(float(ct.grad) - fd) <= 1e-6 * abs(fd)
+
+
+def test_two_argument_step_and_adjoint(torch_cuda):
+    """Plan.step(x, parity) and Plan.adjoint(g, parity) allocate their output
+    and equal the three-argument calls."""
+    torch = torch_cuda
+    from paper_1609_09841_gb300 import Plan
+    m, n = 1, (8, 8, 8)
+    h = (1 / 8,) * 3
+    plan = Plan(m, n, h, 1.0, 0.4 / 8)
+    x = torch.from_numpy(HI.random_state(m, n, seed=23)).cuda()
+    for parity in (0, 1):
+        y = torch.empty_like(x)
+        plan.step(x, y, parity)
+        assert torch.equal(plan.step(x, parity), y)
+        plan.adjoint(x, y, parity)
+        assert torch.equal(plan.adjoint(x, parity), y)
+    with pytest.raises(TypeError):
+        plan.step(x, x)
