@@ -93,15 +93,20 @@ def _time_batch(bplan, a, b, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, starts=BATCH_STARTS, reps=3, sweeps=2):
+def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, starts=BATCH_STARTS, reps=3, sweeps=2,
+               timer=None):
     """Pick and apply the fastest tile shape x z-chunk of every order present
     in a batched plan.  The orders share one persistent launch, so they are
     tuned by coordinate search: from the fastest of the whole z-chunk triples
     `starts` (first tile shapes), each order in turn (heaviest first) has every
     (tile, zchunk) pair timed with the other orders held at their current
     choice, and keeps the fastest; `sweeps` passes over the orders.  Timing:
-    `reps` batched half steps after a warm-up one (CUDA events).  Returns
-    {"tile", "zchunk" (per order 1..3), "ms", "table" (every timing)}."""
+    `reps` batched half steps after a warm-up one (CUDA events), or
+    timer(bplan) if given.  Returns {"tile", "zchunk" (per order 1..3), "ms",
+    "table" (every timing)}."""
+    if timer is None:
+        def timer(p):
+            return _time_batch(p, a, b, reps)
     orders = sorted({s["m"] for s in bplan.sims}, reverse=True)
     tile = [0, 0, 0]
     bplan.set_tiles(tile)
@@ -109,7 +114,7 @@ def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, starts=BAT
     best_ms, zc = None, None
     for z3 in starts:
         bplan.set_schedule(z3)
-        ms = _time_batch(bplan, a, b, reps)
+        ms = timer(bplan)
         table[f"start {list(z3)}"] = ms
         if best_ms is None or ms < best_ms:
             best_ms, zc = ms, list(z3)
@@ -124,7 +129,7 @@ def tune_batch(bplan, a, b, zchunks=BATCH_ZCHUNKS, tiles=BATCH_TILES, starts=BAT
                     tt[m - 1], zz[m - 1] = t, z
                     bplan.set_tiles(tt)
                     bplan.set_schedule(zz)
-                    ms = _time_batch(bplan, a, b, reps)
+                    ms = timer(bplan)
                     table[f"sweep {sweep} m={m} tile={t} zchunk={z}"] = ms
                     if ms < best_ms:
                         best_ms, choice = ms, (t, z)
